@@ -1,0 +1,275 @@
+/*
+ * pargeo_gpu.h — C ABI of the GB300 (sm_103a) kd-tree / BDL-tree k-NN library.
+ *
+ * The library builds kd-trees over Euclidean point sets and answers batched
+ * exact k-nearest-neighbour queries over one tree or over the BDL-tree's
+ * log-structured forest of static trees (ParGeo, Wang et al., ESA 2022:
+ * Section 5 and Appendix A).  It also provides the gradient of the selected
+ * squared distances and a batched multi-cloud Chamfer path.
+ *
+ * Conventions shared by every call
+ *   - Points are float32, row-major: point i occupies p[i*dim .. i*dim+dim-1].
+ *     dim is 1..16.  Coordinates must be finite; squared distances must not
+ *     overflow float32 (|coordinates| well below 1e18).
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *     buffer it passes.  The library copies its inputs and never keeps a
+ *     caller pointer after a call returns.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that take a stream are stream-ordered: they enqueue work and may
+ *     return before it finishes; results are valid once the stream reaches
+ *     them.  Some calls read small counts back to the host and therefore
+ *     synchronise with the stream; each such call says so.
+ *   - k-NN output: per query, k slots ordered by ascending (squared distance,
+ *     index).  out_idx is the data row (trees) or the point id (BDL); out_dist
+ *     is the squared Euclidean distance computed in float32.  When fewer than
+ *     k points are available the remaining slots hold index -1 and +inf.
+ *   - Errors: every call returns a pg_status.  On PG_EINVAL nothing was
+ *     launched and the outputs are untouched.  pg_last_error() describes the
+ *     last failure of the calling thread.
+ */
+#ifndef PARGEO_GPU_H
+#define PARGEO_GPU_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PG_API __attribute__((visibility("default")))
+#else
+#define PG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PG_OK = 0,
+    PG_EINVAL = 1,        /* invalid argument (nothing launched)              */
+    PG_ENOMEM = 2,        /* device or host allocation failed                 */
+    PG_ECUDA = 3,         /* a CUDA runtime call failed                       */
+    PG_ETIMEOUT = 4,      /* a bounded device-side wait gave up               */
+    PG_EUNSUPPORTED = 5   /* valid request this build does not support        */
+} pg_status;
+
+typedef struct pg_tree pg_tree;   /* one static kd-tree (opaque)                */
+typedef struct pg_bdl pg_bdl;     /* one BDL-tree forest (opaque)               */
+
+/* Limits checked by every call. */
+#define PG_MAX_DIM 16
+#define PG_MAX_K 64
+#define PG_MAX_LEAF 256
+#define PG_DEPTH_CAP 48   /* nodes deeper than this become leaves              */
+
+/* ------------------------------------------------------------------------
+ * Static kd-tree (paper Section 5 intro; construction Appendix A.1.1).
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Build a kd-tree over n points (device, n*dim float32).  Every internal node
+ * cuts its tight bounding box in half along its widest dimension (the paper's
+ * spatial-median split, Section 6 "Construction"); a node with at most
+ * leaf_size points, with all points equal, or at depth PG_DEPTH_CAP is a leaf.
+ * n may be 0 (empty tree).  leaf_size in [1, PG_MAX_LEAF]; n < 2^31.
+ * Synchronises with `stream` once per tree level (it reads level sizes).
+ * On success *out receives a handle owned by the caller (free with
+ * pg_tree_free).  Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA.
+ */
+PG_API pg_status pg_tree_build(const float *points, int64_t n, int dim, int leaf_size, void *stream,
+                        pg_tree **out);
+
+/*
+ * Exact k-NN of m query points (device, m*dim float32) against the tree's
+ * points (paper Appendix A.1.3, "Data-Parallel k-NN": every query searched
+ * independently; subtrees whose bounding box is farther than the current k-th
+ * distance are pruned).  queries == NULL means all-kNN: the queries are the
+ * tree's own points and m must equal the tree's n; row i of the output then
+ * belongs to input point i (each point finds itself at distance 0).
+ * out_idx (device, m*k int32) and out_dist (device, m*k float32).
+ * k in [1, PG_MAX_K].  Stream-ordered, no synchronisation.
+ * Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA.
+ */
+PG_API pg_status pg_knn(const pg_tree *tree, const float *queries, int64_t m, int k, int32_t *out_idx,
+                 float *out_dist, void *stream);
+
+/* Release a tree.  Work that uses the tree must be ordered before this call on
+ * the tree's build stream.  NULL is accepted. */
+PG_API pg_status pg_tree_free(pg_tree *tree);
+
+/* Shape of a built tree, for export and inspection. */
+typedef struct {
+    int64_t n;           /* number of points                                   */
+    int32_t dim;         /* coordinate count of the input                      */
+    int32_t dim_class;   /* DC: coordinates stored per point (>= dim, padded 0)*/
+    int32_t leaf_size;
+    int32_t num_nodes;   /* internal nodes                                     */
+    int32_t depth;       /* deepest leaf                                       */
+    int32_t node_floats; /* 32-bit words per node record = 4*DC + 4            */
+    int32_t point_floats;/* 32-bit words per bucket entry = 4*ceil((DC+1)/4)   */
+    int32_t root_ref;    /* root child reference (see pg_tree_export)          */
+    int32_t root_cnt;
+    float root_lo[PG_MAX_DIM]; /* tight box of all points (first dim entries)  */
+    float root_hi[PG_MAX_DIM];
+} pg_tree_info_t;
+
+PG_API pg_status pg_tree_info(const pg_tree *tree, pg_tree_info_t *info);
+
+/*
+ * Copy a tree's layout to host memory (synchronises with the tree's stream).
+ *   nodes      num_nodes * node_floats words.  Node record: float lo0[DC],
+ *              hi0[DC], lo1[DC], hi1[DC] (the tight boxes of the two children),
+ *              then int32 ref0, cnt0, ref1, cnt1.  cnt > 0: the child is a leaf
+ *              holding bucket entries [ref, ref+cnt); cnt == 0: the child is
+ *              the internal node `ref`; cnt < 0: the child holds no live point.
+ *   split_dim  num_nodes int32 and split_val num_nodes float32: the node sends
+ *              x with x[split_dim] < split_val to child 0, the rest to child 1.
+ *   bucket     n * point_floats words: coordinates (DC floats, zero padded)
+ *              with the point's index (int32 bits) at word DC.
+ * Any of the pointers may be NULL to skip that array.
+ */
+PG_API pg_status pg_tree_export(const pg_tree *tree, float *nodes, int32_t *split_dim, float *split_val,
+                         float *bucket);
+
+/* ------------------------------------------------------------------------
+ * BDL-tree (paper Section 5; Appendix A.2 Insert_L, A.3 Erase_L, A.4 kNN_L).
+ * A forest of static kd-trees in slots i = 0, 1, ... with capacity
+ * 2^i * buffer_size plus a buffer tree of capacity buffer_size.
+ * All BDL calls run on the stream given to pg_bdl_create and synchronise with
+ * it (they read counts back to drive the forest bookkeeping).
+ * ---------------------------------------------------------------------- */
+
+/* Create an empty forest.  dim in [1,16], buffer_size (X) >= 1,
+ * leaf_size in [1, PG_MAX_LEAF]. */
+PG_API pg_status pg_bdl_create(int dim, int64_t buffer_size, int leaf_size, void *stream, pg_bdl **out);
+
+/*
+ * Insert a batch of cnt points (device, cnt*dim float32) with Insert_L: the
+ * batch's cnt mod X last points go to the buffer tree; if the buffer then
+ * holds X or more points its X smallest ids join the batch; the full-tree
+ * bitmask becomes F + floor(cnt/X) (+1 on buffer overflow); trees whose bit
+ * clears are destroyed and their live points, with the batch, rebuild the
+ * trees whose bit sets, lowest slot first, each filled to capacity, the
+ * highest new slot taking what remains.
+ * Points receive consecutive ids in input order, continuing from earlier
+ * inserts; out_ids (device, cnt int32, may be NULL) receives them.
+ */
+PG_API pg_status pg_bdl_insert(pg_bdl *bdl, const float *points, int64_t cnt, int32_t *out_ids);
+
+/*
+ * Erase with Erase_L: every live point whose coordinates are bitwise equal to
+ * one of the cnt points (device, cnt*dim float32) is removed from its tree;
+ * then every tree left with fewer than half of its capacity is destroyed and
+ * its live points are reinserted with Insert_L (the buffer tree is exempt).
+ * Points not present are ignored.
+ */
+PG_API pg_status pg_bdl_erase(pg_bdl *bdl, const float *points, int64_t cnt);
+
+/*
+ * Exact k-NN of m queries over the whole forest: one k-buffer per query is
+ * carried across every non-empty tree (kNN_L), so the answer is the k-NN of
+ * the live point set.  out_idx holds point ids.  Arguments as in pg_knn
+ * (queries must not be NULL).
+ */
+PG_API pg_status pg_bdl_knn(const pg_bdl *bdl, const float *queries, int64_t m, int k, int32_t *out_idx,
+                     float *out_dist);
+
+/* Number of live points. */
+PG_API pg_status pg_bdl_size(const pg_bdl *bdl, int64_t *live);
+
+/*
+ * Forest bookkeeping, to host memory: *F = bitmask of occupied slots,
+ * slot_live[i] (64 entries) = live points of slot i (0 when empty),
+ * *buffer_live = live points in the buffer tree, *next_id = ids handed out.
+ */
+PG_API pg_status pg_bdl_structure(const pg_bdl *bdl, uint64_t *F, int64_t *slot_live,
+                           int64_t *buffer_live, int64_t *next_id);
+
+/* Where every id lives, to host memory (next_id int8 entries): slot index,
+ * -2 for the buffer tree, -1 for erased ids. */
+PG_API pg_status pg_bdl_slot_of(const pg_bdl *bdl, int8_t *slot_of);
+
+PG_API pg_status pg_bdl_free(pg_bdl *bdl);
+
+/* ------------------------------------------------------------------------
+ * Gradient (not in the paper: derivative of the selected squared distances).
+ * ---------------------------------------------------------------------- */
+
+/*
+ * For L = sum_{i<m, j<k} grad_dist[i*k+j] * |q_i - p_{idx[i*k+j]}|^2:
+ *   grad_queries[i]  = sum_j 2 g_ij (q_i - p_idx(i,j))            (m*dim)
+ *   grad_data[t]     = -sum_{(i,j): idx_ij = t} 2 g_ij (q_i - p_t) (n*dim)
+ * Distances are recomputed from the coordinates (float32).  Entries with
+ * idx < 0 are skipped.  grad_data is summed per data point in ascending
+ * (i, j) order after a stable sort by index, so the result is bitwise
+ * deterministic.  All pointers are device memory; either gradient may be
+ * NULL.  Outputs are overwritten (not accumulated).  Stream-ordered.
+ */
+PG_API pg_status pg_knn_backward(const float *data, int64_t n, const float *queries, int64_t m, int dim,
+                          int k, const int32_t *idx, const float *grad_dist, float *grad_queries,
+                          float *grad_data, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched multi-cloud Chamfer path (not in the paper: many uneven point
+ * clouds built and queried in one persistent launch over a work queue).
+ * ---------------------------------------------------------------------- */
+
+/*
+ * npairs cloud pairs.  a (device, a_off[npairs]*dim) holds the A clouds back
+ * to back; a_off (HOST, npairs+1 int64) their row offsets; likewise b/b_off.
+ * For every pair i and both directions it finds the k nearest neighbours of
+ * each point of A_i in B_i and of each point of B_i in A_i, and writes
+ *   loss[i]  (device, npairs float32) = sum of the selected squared distances
+ *   idx_ab   (device, |a|*k int32)   neighbour rows local to B_i
+ *   idx_ba   (device, |b|*k int32)   neighbour rows local to A_i
+ *   dist_ab / dist_ba (device float32, same shapes; may be NULL)
+ * leaf_size as in pg_tree_build.  Each cloud must hold >= 1 point.
+ * Stream-ordered (the plan is cached per (offsets, dim, k, leaf_size)).
+ */
+PG_API pg_status pg_batched_chamfer(const float *a, const int64_t *a_off, const float *b,
+                             const int64_t *b_off, int npairs, int dim, int k, int leaf_size,
+                             float *loss, int32_t *idx_ab, int32_t *idx_ba, float *dist_ab,
+                             float *dist_ba, void *stream);
+
+/*
+ * Backward twin: given upstream dL/dloss[i] (device, npairs float32) and the
+ * indices written by pg_batched_chamfer, writes grad_a (|a|*dim) and grad_b
+ * (|b|*dim), float32, device, deterministic as in pg_knn_backward.
+ */
+PG_API pg_status pg_batched_chamfer_backward(const float *a, const int64_t *a_off, const float *b,
+                                      const int64_t *b_off, int npairs, int dim, int k,
+                                      const int32_t *idx_ab, const int32_t *idx_ba,
+                                      const float *grad_loss, float *grad_a, float *grad_b,
+                                      void *stream);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics.
+ * ---------------------------------------------------------------------- */
+
+/* Message of the calling thread's last failure ("" if none). */
+PG_API const char *pg_last_error(void);
+
+/* Library version string. */
+PG_API const char *pg_version(void);
+
+/* Number of kernels this library has launched in this process. */
+PG_API uint64_t pg_launch_count(void);
+
+/*
+ * Kernel timing: while enabled, the library brackets each launch of the
+ * kernels it times with CUDA events on the launching stream.
+ * pg_profile_read synchronises, then returns the summed milliseconds and the
+ * launch count recorded for kernels whose name starts with `prefix`, and
+ * clears them.
+ */
+PG_API pg_status pg_profile_enable(int on);
+PG_API pg_status pg_profile_read(const char *prefix, double *total_ms, int64_t *launches);
+
+/* Fault injection for tests: the n-th device allocation from now fails with
+ * PG_ENOMEM (n <= 0 disables).  Host-side only; no GPU fault is involved. */
+PG_API pg_status pg_debug_fail_alloc_after(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARGEO_GPU_H */

@@ -1,0 +1,519 @@
+// kd-tree construction on the GPU (paper Section 5 intro and Appendix A.1.1;
+// spatial-median split of Section 6 "Construction").
+//
+// Level-synchronous top-down build.  At every level each active segment (a
+// contiguous range of the point array holding one node's points) is
+// classified as a leaf or split at the midpoint of its tight bounding box in
+// its widest dimension.  All points of split segments are then partitioned
+// stably in one pass: a device-wide exclusive scan of the "goes left" flags
+// gives every point its destination, because each segment is contiguous
+// (left rank = scan[i] - scan[segment start]).  The same pass reduces the two
+// children's tight boxes with warp-aggregated integer atomics on an
+// order-preserving float encoding.  The node that a segment becomes is
+// numbered by a scan over the level's split flags, so the layout is
+// deterministic.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace pg {
+
+namespace {
+
+constexpr int BT = 256;
+
+__device__ __forceinline__ float *rec_of(float4 *nodes, int node, int dc) {
+    return reinterpret_cast<float *>(nodes + (size_t)node * node_w(dc));
+}
+
+__global__ void k_init_box(int *lo, int *hi, int count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        lo[i] = 0x7f800000;                 // f2o(+inf)
+        hi[i] = (int)0x807fffffu;           // f2o(-inf)
+    }
+}
+
+// Pack rows into bucket entries (coordinates zero padded to DC, id at word
+// DC) and reduce the root box.
+template <int DC>
+__global__ void __launch_bounds__(BT) k_pack(const float *__restrict__ src, const int32_t *__restrict__ rows,
+                                             const int32_t *__restrict__ ids, int64_t n, int dim,
+                                             float4 *__restrict__ out, int *__restrict__ box_lo,
+                                             int *__restrict__ box_hi) {
+    constexpr int W = bucket_w(DC);
+    float lo[DC], hi[DC];
+#pragma unroll
+    for (int c = 0; c < DC; ++c) { lo[c] = __int_as_float(0x7f800000); hi[c] = -lo[c]; }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = rows ? (int64_t)rows[i] : i;
+        float v[4 * W];
+#pragma unroll
+        for (int c = 0; c < 4 * W; ++c) v[c] = 0.f;
+#pragma unroll
+        for (int c = 0; c < DC; ++c)
+            if (c < dim) v[c] = src[row * dim + c];
+        v[DC] = __int_as_float(ids ? ids[i] : (int)i);
+#pragma unroll
+        for (int w = 0; w < W; ++w) out[i * W + w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
+#pragma unroll
+        for (int c = 0; c < DC; ++c) { lo[c] = fminf(lo[c], v[c]); hi[c] = fmaxf(hi[c], v[c]); }
+    }
+    __shared__ int s_lo[BT / 32][DC], s_hi[BT / 32][DC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < DC; ++c) {
+        int a = __reduce_min_sync(0xffffffffu, f2o(lo[c]));
+        int b = __reduce_max_sync(0xffffffffu, f2o(hi[c]));
+        if (lane == 0) { s_lo[warp][c] = a; s_hi[warp][c] = b; }
+    }
+    __syncthreads();
+    if (threadIdx.x < DC) {
+        int a = INT_MAX, b = INT_MIN;
+        for (int w = 0; w < BT / 32; ++w) { a = min(a, s_lo[w][threadIdx.x]); b = max(b, s_hi[w][threadIdx.x]); }
+        atomicMin(&box_lo[threadIdx.x], a);
+        atomicMax(&box_hi[threadIdx.x], b);
+    }
+}
+
+// Decide, per segment, leaf or split; for a split pick the widest dimension
+// of the tight box (lowest index on ties) and its midpoint.
+template <int DC>
+__global__ void k_classify(int S, const int *__restrict__ start, const int *__restrict__ end,
+                           const int *__restrict__ depth, const int *__restrict__ lo,
+                           const int *__restrict__ hi, int leaf, int depth_cap, int *__restrict__ split_flag,
+                           int *__restrict__ sdim, float *__restrict__ sval) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int size = end[s] - start[s];
+    int flag = 0, bd = 0;
+    float bv = 0.f;
+    if (size > leaf && depth[s] < depth_cap) {
+        float best = 0.f;
+#pragma unroll
+        for (int c = 0; c < DC; ++c) {
+            float e = __fsub_rn(o2f(hi[s * DC + c]), o2f(lo[s * DC + c]));
+            if (e > best) { best = e; bd = c; }
+        }
+        if (best > 0.f) {
+            const float l = o2f(lo[s * DC + bd]), h = o2f(hi[s * DC + bd]);
+            float mid = __fadd_rn(__fmul_rn(0.5f, l), __fmul_rn(0.5f, h));
+            if (!(mid > l)) mid = h;
+            if (mid > h) mid = h;
+            flag = 1;
+            bv = mid;
+        }
+    }
+    split_flag[s] = flag;
+    sdim[s] = bd;
+    sval[s] = bv;
+}
+
+// Write each segment into its parent's child slot (tight box + reference),
+// record split nodes and prepare the next level's child segments.
+template <int DC>
+__global__ void k_link(int S, const int *__restrict__ start, const int *__restrict__ end,
+                       const int *__restrict__ parent, const int *__restrict__ side,
+                       const int *__restrict__ depth, const int *__restrict__ lo, const int *__restrict__ hi,
+                       const int *__restrict__ split_flag, const int *__restrict__ split_rank,
+                       const int *__restrict__ sdim, const float *__restrict__ sval, int node_base,
+                       float4 *__restrict__ nodes, int *__restrict__ n_sdim, float *__restrict__ n_sval,
+                       int2 *__restrict__ n_range, int *__restrict__ nx_parent, int *__restrict__ nx_side,
+                       int *__restrict__ nx_depth, int *__restrict__ nx_lo, int *__restrict__ nx_hi) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int st = start[s], size = end[s] - st;
+    const int p = parent[s];
+    const bool split = split_flag[s] != 0;
+    const int node = node_base + split_rank[s];
+    if (p >= 0) {
+        float *rec = rec_of(nodes, p, DC);
+        const int c = side[s];
+#pragma unroll
+        for (int d = 0; d < DC; ++d) {
+            rec[c * 2 * DC + d] = o2f(lo[s * DC + d]);
+            rec[c * 2 * DC + DC + d] = o2f(hi[s * DC + d]);
+        }
+        int *ri = reinterpret_cast<int *>(rec + 4 * DC);
+        ri[2 * c] = split ? node : st;
+        ri[2 * c + 1] = split ? 0 : size;
+    }
+    if (split) {
+        n_sdim[node] = sdim[s];
+        n_sval[node] = sval[s];
+        n_range[node] = make_int2(st, st + size);
+        const int r = split_rank[s];
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            const int x = 2 * r + ch;
+            nx_parent[x] = node;
+            nx_side[x] = ch;
+            nx_depth[x] = depth[s] + 1;
+#pragma unroll
+            for (int d = 0; d < DC; ++d) {
+                nx_lo[x * DC + d] = 0x7f800000;
+                nx_hi[x * DC + d] = (int)0x807fffffu;
+            }
+        }
+    }
+}
+
+template <int DC>
+__global__ void __launch_bounds__(BT) k_flag(int64_t n, const float4 *__restrict__ P,
+                                             const int *__restrict__ seg_of, const int *__restrict__ split_flag,
+                                             const int *__restrict__ sdim, const float *__restrict__ sval,
+                                             int *__restrict__ flag) {
+    constexpr int W = bucket_w(DC);
+    const float *pf = reinterpret_cast<const float *>(P);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = seg_of[i];
+        int f = 0;
+        if (s >= 0 && split_flag[s]) f = pf[i * 4 * W + sdim[s]] < sval[s];
+        flag[i] = f;
+    }
+}
+
+// Stable partition of every split segment + child tight boxes.
+template <int DC>
+__global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
+                                                const int *__restrict__ seg_of, int *__restrict__ seg_of_nx,
+                                                const int *__restrict__ start, const int *__restrict__ end,
+                                                const int *__restrict__ split_flag,
+                                                const int *__restrict__ split_rank, const int *__restrict__ pre,
+                                                int *__restrict__ nx_start, int *__restrict__ nx_end,
+                                                int *__restrict__ nx_lo, int *__restrict__ nx_hi) {
+    constexpr int W = bucket_w(DC);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < n;
+        int child = -1;
+        int64_t dst = i;
+        float4 v[W];
+        if (valid) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) v[w] = P[i * W + w];
+            const int s = seg_of[i];
+            if (s >= 0 && split_flag[s]) {
+                const int st = start[s], en = end[s];
+                const int b0 = pre[st];
+                const int nl = pre[en] - b0;
+                const int r = pre[i] - b0;
+                const int f = pre[i + 1] - pre[i];
+                const int rk = split_rank[s];
+                if (f) { dst = st + r; child = 2 * rk; }
+                else { dst = st + nl + (int)(i - st) - r; child = 2 * rk + 1; }
+                if (i == st) {
+                    nx_start[2 * rk] = st;
+                    nx_end[2 * rk] = st + nl;
+                    nx_start[2 * rk + 1] = st + nl;
+                    nx_end[2 * rk + 1] = en;
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) Q[dst * W + w] = v[w];
+            seg_of_nx[dst] = child;
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) v[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float *cf = reinterpret_cast<const float *>(v);
+        unsigned active = __ballot_sync(0xffffffffu, child >= 0);
+        while (active) {
+            const int leader = __ffs(active) - 1;
+            const int key = __shfl_sync(0xffffffffu, child, leader);
+            const bool mine = child == key;
+            const unsigned grp = __ballot_sync(0xffffffffu, mine);
+#pragma unroll
+            for (int d = 0; d < DC; ++d) {
+                const int e = f2o(cf[d]);
+                const int a = __reduce_min_sync(0xffffffffu, mine ? e : INT_MAX);
+                const int b = __reduce_max_sync(0xffffffffu, mine ? e : INT_MIN);
+                if (lane == leader) {
+                    atomicMin(&nx_lo[key * DC + d], a);
+                    atomicMax(&nx_hi[key * DC + d], b);
+                }
+            }
+            active &= ~grp;
+        }
+    }
+}
+
+struct Segs {
+    int *start, *end, *parent, *side, *depth, *lo, *hi;
+};
+
+template <int DC>
+struct Builder {
+    static pg_status run(float4 *packed, int *box, int64_t n, int leaf, cudaStream_t s, pg_tree *t);
+};
+
+pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
+    if (need <= t->node_cap) return PG_OK;
+    int cap = std::max(need, std::max(16, t->node_cap * 2));
+    const int nw = node_w(t->dc);
+    float4 *nodes;
+    int *sd;
+    float *sv;
+    int2 *rg;
+    PG_TRY(dalloc_n(&nodes, (size_t)cap * nw, s));
+    if (dalloc_n(&sd, cap, s) != PG_OK) { dfree(nodes, s); return PG_ENOMEM; }
+    if (dalloc_n(&sv, cap, s) != PG_OK) { dfree(nodes, s); dfree(sd, s); return PG_ENOMEM; }
+    if (dalloc_n(&rg, cap, s) != PG_OK) { dfree(nodes, s); dfree(sd, s); dfree(sv, s); return PG_ENOMEM; }
+    if (t->num_nodes > 0) {
+        PG_CUDA(cudaMemcpyAsync(nodes, t->nodes, sizeof(float4) * nw * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(sd, t->split_dim, sizeof(int) * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(sv, t->split_val, sizeof(float) * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(rg, t->node_range, sizeof(int2) * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
+    }
+    dfree(t->nodes, s);
+    dfree(t->split_dim, s);
+    dfree(t->split_val, s);
+    dfree(t->node_range, s);
+    t->nodes = nodes;
+    t->split_dim = sd;
+    t->split_val = sv;
+    t->node_range = rg;
+    t->node_cap = cap;
+    return PG_OK;
+}
+
+template <int DC>
+pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream_t s, pg_tree *t) {
+    constexpr int W = bucket_w(DC);
+    const int grid_pts = std::max(1, std::min(ceil_div_i(n, BT), num_sms() * 8));
+    // Split segments hold more than `leaf` points and are disjoint, so a level
+    // has at most 2*floor(n/(leaf+1)) segments.
+    const int seg_cap = (int)std::max<int64_t>(2, 2 * (n / (leaf + 1)) + 2);
+
+    Scratch sP1, sSeg0, sSeg1, sFlag, sPre, sSegA, sSegB, sLvl, sHost;
+    PG_TRY(sP1.alloc(sizeof(float4) * W * (size_t)n, s));
+    PG_TRY(sSeg0.alloc(sizeof(int) * (size_t)n, s));
+    PG_TRY(sSeg1.alloc(sizeof(int) * (size_t)n, s));
+    PG_TRY(sFlag.alloc(sizeof(int) * (size_t)n, s));
+    PG_TRY(sPre.alloc(sizeof(int) * (size_t)(n + 1), s));
+    const size_t seg_words = (size_t)seg_cap * (5 + 2 * DC);
+    PG_TRY(sSegA.alloc(sizeof(int) * seg_words, s));
+    PG_TRY(sSegB.alloc(sizeof(int) * seg_words, s));
+    // per-level: split_flag, split_rank (+1), sdim, sval
+    PG_TRY(sLvl.alloc(sizeof(int) * (size_t)(4 * seg_cap + 1), s));
+    int *split_flag = sLvl.as<int>();
+    int *split_rank = split_flag + seg_cap;
+    int *sdim = split_rank + seg_cap + 1;
+    float *sval = reinterpret_cast<float *>(sdim + seg_cap);
+
+    auto carve = [&](Scratch &sc) {
+        int *b = sc.as<int>();
+        Segs g;
+        g.start = b; g.end = b + seg_cap; g.parent = b + 2 * seg_cap; g.side = b + 3 * seg_cap;
+        g.depth = b + 4 * seg_cap; g.lo = b + 5 * seg_cap; g.hi = b + (5 + DC) * seg_cap;
+        return g;
+    };
+    Segs cur = carve(sSegA), nxt = carve(sSegB);
+
+    float4 *P = P0, *Q = sP1.as<float4>();
+    int *seg_of = sSeg0.as<int>(), *seg_of_nx = sSeg1.as<int>();
+    PG_CUDA(cudaMemsetAsync(seg_of, 0, sizeof(int) * (size_t)n, s));   // all in segment 0
+
+    // level 0: one segment covering everything, box reduced by k_pack
+    {
+        int h[5] = {0, (int)n, -1, 0, 0};
+        PG_CUDA(cudaMemcpyAsync(cur.start, &h[0], sizeof(int), cudaMemcpyHostToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(cur.end, &h[1], sizeof(int), cudaMemcpyHostToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(cur.parent, &h[2], sizeof(int), cudaMemcpyHostToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(cur.side, &h[3], sizeof(int), cudaMemcpyHostToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(cur.depth, &h[4], sizeof(int), cudaMemcpyHostToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(cur.lo, box, sizeof(int) * DC, cudaMemcpyDeviceToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(cur.hi, box + DC, sizeof(int) * DC, cudaMemcpyDeviceToDevice, s));
+    }
+    int hT[1] = {0};
+
+    int S = 1;
+    int level = 0;
+    int node_base = 0;
+    bool root_split = false;
+    t->num_nodes = 0;
+    for (;;) {
+        const int gs = ceil_div_i(S, BT);
+        k_classify<DC><<<gs, BT, 0, s>>>(S, cur.start, cur.end, cur.depth, cur.lo, cur.hi, leaf, PG_DEPTH_CAP,
+                                         split_flag, sdim, sval);
+        count_launch();
+        PG_TRY(exclusive_scan(split_flag, split_rank, S, s));
+        PG_CUDA(cudaMemcpyAsync(hT, split_rank + S, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+        const int T = *hT;
+        if (level == 0) root_split = T > 0;
+        PG_TRY(grow_nodes(t, node_base + T, s));
+        k_link<DC><<<gs, BT, 0, s>>>(S, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo, cur.hi,
+                                     split_flag, split_rank, sdim, sval, node_base, t->nodes, t->split_dim,
+                                     t->split_val, t->node_range, nxt.parent, nxt.side, nxt.depth, nxt.lo,
+                                     nxt.hi);
+        count_launch();
+        PG_TRY(check_launch("build level"));
+        if (T == 0) break;
+        k_flag<DC><<<grid_pts, BT, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, sFlag.as<int>());
+        count_launch();
+        PG_TRY(exclusive_scan(sFlag.as<int>(), sPre.as<int>(), n, s));
+        {
+            KTimer kt("build_scatter", s);
+            k_scatter<DC><<<grid_pts, BT, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
+                                                  split_rank, sPre.as<int>(), nxt.start, nxt.end, nxt.lo, nxt.hi);
+            count_launch();
+        }
+        PG_TRY(check_launch("build scatter"));
+        node_base += T;
+        t->num_nodes = node_base;
+        std::swap(P, Q);
+        std::swap(seg_of, seg_of_nx);
+        std::swap(cur, nxt);
+        S = 2 * T;
+        ++level;
+    }
+    t->depth = level;
+    t->root_ref = 0;
+    t->root_cnt = root_split ? 0 : (int)n;
+    // The final array becomes the bucket; the other ping-pong buffer is freed.
+    if (P == P0) {
+        t->bucket = P0;
+    } else {
+        t->bucket = P;
+        sP1.p = nullptr;           // ownership moves to the tree
+        dfree(P0, s);
+    }
+    return PG_OK;
+}
+
+template <int DC>
+pg_status pack_impl(const float *src, const int32_t *rows, const int32_t *ids, int64_t n, int dim, float4 *out,
+                    int *box, cudaStream_t s) {
+    k_init_box<<<1, 64, 0, s>>>(box, box + DC, DC);
+    count_launch();
+    if (n > 0) {
+        const int grid = std::max(1, std::min(ceil_div_i(n, BT), num_sms() * 4));
+        k_pack<DC><<<grid, BT, 0, s>>>(src, rows, ids, n, dim, out, box, box + DC);
+        count_launch();
+    }
+    return check_launch("pack");
+}
+
+}  // namespace
+
+#define PG_DC_SWITCH(dc, CALL)                                   \
+    switch (dc) {                                                \
+        case 2: { constexpr int DCV = 2; CALL; } break;          \
+        case 3: { constexpr int DCV = 3; CALL; } break;          \
+        case 4: { constexpr int DCV = 4; CALL; } break;          \
+        case 5: { constexpr int DCV = 5; CALL; } break;          \
+        case 6: { constexpr int DCV = 6; CALL; } break;          \
+        case 7: { constexpr int DCV = 7; CALL; } break;          \
+        case 8: { constexpr int DCV = 8; CALL; } break;          \
+        case 12: { constexpr int DCV = 12; CALL; } break;        \
+        case 16: { constexpr int DCV = 16; CALL; } break;        \
+        default: return fail(PG_EUNSUPPORTED, "dimension class"); \
+    }
+
+// Packs and builds in one go (the packed array is allocated here).
+static pg_status build_from(const float *src, const int32_t *rows, const int32_t *ids, int64_t n, int dim,
+                            int leaf, cudaStream_t s, pg_tree *t) {
+    const int dc = dim_class(dim);
+    t->n = n;
+    t->dim = dim;
+    t->dc = dc;
+    t->leaf_size = leaf;
+    t->stream = s;
+    t->live = n;
+    if (n == 0) {
+        t->root_ref = -1;
+        t->root_cnt = -1;
+        t->num_nodes = 0;
+        t->depth = 0;
+        return tree_upload_desc(t);
+    }
+    const int W = bucket_w(dc);
+    float4 *packed = nullptr;
+    PG_TRY(dalloc_n(&packed, (size_t)W * n, s));
+    Scratch box;
+    if (box.alloc(sizeof(int) * 2 * PG_MAX_DIM, s) != PG_OK) {
+        dfree(packed, s);
+        return PG_ENOMEM;
+    }
+    pg_status st = PG_OK;
+    PG_DC_SWITCH(dc, st = pack_impl<DCV>(src, rows, ids, n, dim, packed, box.as<int>(), s));
+    if (st != PG_OK) { dfree(packed, s); return st; }
+    int hbox[2 * PG_MAX_DIM];
+    PG_CUDA(cudaMemcpyAsync(hbox, box.as<int>(), sizeof(int) * 2 * dc, cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < PG_MAX_DIM; ++c) { t->root_lo[c] = 0.f; t->root_hi[c] = 0.f; }
+    for (int c = 0; c < dc; ++c) {
+        int a = hbox[c], b = hbox[dc + c];
+        a = a >= 0 ? a : (a ^ 0x7fffffff);
+        b = b >= 0 ? b : (b ^ 0x7fffffff);
+        float fa, fb;
+        memcpy(&fa, &a, 4);
+        memcpy(&fb, &b, 4);
+        t->root_lo[c] = fa;
+        t->root_hi[c] = fb;
+        if (!std::isfinite(fa) || !std::isfinite(fb)) {
+            dfree(packed, s);
+            return fail(PG_EINVAL, "points must have finite coordinates");
+        }
+    }
+    PG_DC_SWITCH(dc, st = Builder<DCV>::run(packed, box.as<int>(), n, leaf, s, t));
+    if (st != PG_OK) {
+        if (t->bucket != packed) dfree(packed, s);
+        return st;
+    }
+    return tree_upload_desc(t);
+}
+
+pg_status build_rows(const float *pts, int64_t n, int dim, int leaf, cudaStream_t s, pg_tree *t) {
+    return build_from(pts, nullptr, nullptr, n, dim, leaf, s, t);
+}
+
+pg_status build_gather(const float *store, const int32_t *ids, int64_t n, int dim, int leaf, cudaStream_t s,
+                       pg_tree *t) {
+    return build_from(store, ids, ids, n, dim, leaf, s, t);
+}
+
+TreeDesc tree_desc(const pg_tree *t) {
+    TreeDesc d;
+    memset(&d, 0, sizeof(d));
+    d.bucket = t->bucket;
+    d.nodes = t->nodes;
+    d.root_ref = t->root_ref;
+    d.root_cnt = t->root_cnt;
+    for (int c = 0; c < PG_MAX_DIM; ++c) { d.root_lo[c] = t->root_lo[c]; d.root_hi[c] = t->root_hi[c]; }
+    return d;
+}
+
+pg_status tree_upload_desc(pg_tree *t) {
+    if (!t->desc) PG_TRY(dalloc_n(&t->desc, 1, t->stream));
+    TreeDesc d = tree_desc(t);
+    PG_CUDA(cudaMemcpyAsync(t->desc, &d, sizeof(d), cudaMemcpyHostToDevice, t->stream));
+    PG_CUDA(cudaStreamSynchronize(t->stream));
+    return PG_OK;
+}
+
+void tree_release(pg_tree *t) {
+    cudaStream_t s = t->stream;
+    dfree(t->bucket, s);
+    dfree(t->nodes, s);
+    dfree(t->split_dim, s);
+    dfree(t->split_val, s);
+    dfree(t->node_range, s);
+    dfree(t->desc, s);
+    t->bucket = nullptr;
+    t->nodes = nullptr;
+    t->split_dim = nullptr;
+    t->split_val = nullptr;
+    t->node_range = nullptr;
+    t->desc = nullptr;
+}
+
+}  // namespace pg

@@ -1,0 +1,60 @@
+// Internal structures and host-side launchers shared by the library's
+// translation units.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+struct pg_tree {
+    int64_t n = 0;
+    int dim = 0;
+    int dc = 2;
+    int leaf_size = 16;
+    int num_nodes = 0;
+    int node_cap = 0;
+    int depth = 0;
+    int root_ref = -1;
+    int root_cnt = -1;           // >0 leaf root, 0 internal root, <0 empty
+    float root_lo[PG_MAX_DIM] = {0};
+    float root_hi[PG_MAX_DIM] = {0};
+    float4 *bucket = nullptr;    // n * bucket_w(dc)
+    float4 *nodes = nullptr;     // node_cap * node_w(dc)
+    int *split_dim = nullptr;    // node_cap
+    float *split_val = nullptr;  // node_cap
+    int2 *node_range = nullptr;  // node_cap: bucket range [x, y) of the node
+    pg::TreeDesc *desc = nullptr;  // device copy of this tree's descriptor
+    cudaStream_t stream = nullptr;
+    int64_t live = 0;            // live points (BDL trees lose points on erase)
+};
+
+namespace pg {
+
+// ---- scan.cu
+// out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total.
+pg_status exclusive_scan(const int *in, int *out, int64_t n, cudaStream_t s);
+
+// ---- build.cu
+// Pack row-major points (n*dim) into bucket entries with ids (ids == NULL: i).
+pg_status pack_points(const float *pts, const int32_t *ids, int64_t n, int dim, int dc,
+                      float4 *out, cudaStream_t s);
+// Gather rows of a row-major store by id list into bucket entries.
+pg_status gather_points(const float *store, const int32_t *ids, int64_t n, int dim, int dc,
+                        float4 *out, cudaStream_t s);
+// Build a tree over packed bucket entries.  Takes ownership of `packed`
+// (it becomes the tree's bucket array or is freed).
+pg_status build_packed(float4 *packed, int64_t n, int dim, int leaf, cudaStream_t s, pg_tree *t);
+void tree_release(pg_tree *t);
+pg_status tree_upload_desc(pg_tree *t);
+TreeDesc tree_desc(const pg_tree *t);
+
+// ---- knn_dispatch.cu
+// k-NN over `ntrees` trees described in device memory.  If self_bucket is not
+// NULL the queries are the m bucket entries of that array and the output row
+// is the entry's id; otherwise queries are row-major m*dim floats.
+pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
+                     const float4 *self_bucket, int64_t m, int dim, int k, int32_t *out_idx,
+                     float *out_dist, cudaStream_t s);
+int k_class(int k);
+
+}  // namespace pg

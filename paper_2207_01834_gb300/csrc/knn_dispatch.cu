@@ -1,0 +1,41 @@
+// Chooses the traversal kernel instance for a (dimension class, k) request.
+#include "internal.h"
+
+namespace pg {
+
+#define PG_DECL(DCN)                                                                                      \
+    pg_status knn_launch_dc##DCN(const TreeDesc *, int, const float *, const float4 *, int64_t, int, int, \
+                                 int32_t *, float *, cudaStream_t);
+PG_DECL(2) PG_DECL(3) PG_DECL(4) PG_DECL(5) PG_DECL(6) PG_DECL(7) PG_DECL(8) PG_DECL(12) PG_DECL(16)
+#undef PG_DECL
+
+int k_class(int k) {
+    if (k <= 1) return 1;
+    if (k <= 2) return 2;
+    if (k <= 4) return 4;
+    if (k <= 8) return 8;
+    if (k <= 10) return 10;
+    if (k <= 16) return 16;
+    if (k <= 32) return 32;
+    return 64;
+}
+
+pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
+                     const float4 *self_bucket, int64_t m, int dim, int k, int32_t *out_idx, float *out_dist,
+                     cudaStream_t s) {
+    if (m == 0) return PG_OK;
+    switch (dc) {
+        case 2: return knn_launch_dc2(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 3: return knn_launch_dc3(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 4: return knn_launch_dc4(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 5: return knn_launch_dc5(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 6: return knn_launch_dc6(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 7: return knn_launch_dc7(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 8: return knn_launch_dc8(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 12: return knn_launch_dc12(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 16: return knn_launch_dc16(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        default: return fail(PG_EUNSUPPORTED, "dimension class");
+    }
+}
+
+}  // namespace pg

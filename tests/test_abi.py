@@ -1,0 +1,83 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares, and
+argument validation rejects bad calls before any launch (no GPU needed)."""
+from __future__ import annotations
+
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(pg_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2207_01834_gb300.build import build
+    from paper_2207_01834_gb300 import _lib
+
+    build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert {"pg_tree_build", "pg_knn", "pg_bdl_insert", "pg_bdl_erase", "pg_knn_backward"} <= declared
+    for name in sorted(declared):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_binding_covers_every_symbol(lib):
+    from paper_2207_01834_gb300 import _lib
+
+    assert _declared() == set(_lib.SIGNATURES)
+
+
+def test_version_and_counters(lib):
+    assert b"sm_103a" in lib.pg_version()
+    assert lib.pg_launch_count() >= 0
+
+
+def _status(lib, name, *args):
+    return getattr(lib, name)(*args)
+
+
+def test_invalid_arguments_rejected_without_launch(lib):
+    out = C.c_void_p()
+    fake = C.c_void_p(0x1000)   # never dereferenced: validation fails first
+    before = lib.pg_launch_count()
+    assert _status(lib, "pg_tree_build", fake, 10, 0, 16, None, C.byref(out)) == 1        # dim 0
+    assert _status(lib, "pg_tree_build", fake, 10, 17, 16, None, C.byref(out)) == 1       # dim 17
+    assert _status(lib, "pg_tree_build", fake, -1, 3, 16, None, C.byref(out)) == 1        # n < 0
+    assert _status(lib, "pg_tree_build", fake, 1 << 31, 3, 16, None, C.byref(out)) == 1   # n >= 2^31
+    assert _status(lib, "pg_tree_build", fake, 10, 3, 0, None, C.byref(out)) == 1         # leaf 0
+    assert _status(lib, "pg_tree_build", fake, 10, 3, 257, None, C.byref(out)) == 1       # leaf > 256
+    assert _status(lib, "pg_tree_build", None, 10, 3, 16, None, C.byref(out)) == 1        # NULL points
+    assert _status(lib, "pg_tree_build", fake, 10, 3, 16, None, None) == 1                # NULL out
+    assert b"leaf_size" in lib.pg_last_error() or b"out" in lib.pg_last_error()
+    assert _status(lib, "pg_knn", None, fake, 10, 5, fake, fake, None) == 1              # NULL tree
+    assert _status(lib, "pg_bdl_create", 0, 64, 16, None, C.byref(out)) == 1             # dim 0
+    assert _status(lib, "pg_bdl_create", 3, 0, 16, None, C.byref(out)) == 1             # X = 0
+    assert _status(lib, "pg_knn_backward", fake, 10, fake, 10, 3, 0, fake, fake, fake, fake, None) == 1  # k=0
+    assert lib.pg_launch_count() == before
+
+
+def test_header_documents_every_entry_point():
+    """Each declaration in the header is preceded by a comment."""
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        lines = open(h).read().splitlines()
+        for i, line in enumerate(lines):
+            m = re.match(r"PG_API .*\b(pg_\w+)\(", line)
+            if m:
+                prev = "\n".join(lines[max(0, i - 30):i])
+                assert "*/" in prev, f"{m.group(1)} has no comment"

@@ -1,0 +1,186 @@
+"""GPU parity of the static kd-tree path: build invariants and k-NN against the
+CPU oracle, called through the C ABI (via the thin binding)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from knn_compare import compare_knn
+from oracle.kdtree_check import check_tree
+from paper_2207_01834_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_01834_gb300 import api as a
+    return a
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _chain_1d(n):
+    # x_i = 2^-i: every midpoint split peels one point off, so the tree hits the depth cap
+    return (2.0 ** -np.arange(n, dtype=np.float64)).astype(np.float32)[:, None]
+
+
+TREE_CASES = {
+    "uniform2d": (lambda: synth.uniform(20000, 2, 1), 16),
+    "uniform3d_leaf8": (lambda: synth.uniform(50000, 3, 2), 8),
+    "gmm5d_leaf32": (lambda: synth.gmm(30000, 5, 3), 32),
+    "gmm7d": (lambda: synth.gmm(30000, 7, 4), 16),
+    "dim1": (lambda: synth.uniform(5000, 1, 5), 4),
+    "dim10": (lambda: synth.uniform(8000, 10, 6), 16),
+    "dim16": (lambda: synth.gmm(8000, 16, 7), 16),
+    "all_equal": (lambda: np.full((1000, 3), 0.25, np.float32), 16),
+    "collinear": (lambda: np.repeat(synth.uniform(3000, 1, 8), 3, axis=1), 16),
+    "one_point": (lambda: synth.uniform(1, 3, 9), 16),
+    "below_leaf": (lambda: synth.uniform(5, 3, 10), 16),
+    "duplicates": (lambda: np.repeat(synth.uniform(500, 3, 11), 7, axis=0), 4),
+    "lattice3d": (lambda: synth.lattice((20, 20, 20)), 16),
+    "depth_cap_chain": (lambda: _chain_1d(120), 1),
+    "leaf1": (lambda: synth.uniform(3000, 2, 12), 1),
+    "negative_coords": (lambda: synth.uniform(4000, 3, 13) - 0.5, 16),
+}
+
+
+@pytest.mark.parametrize("case", sorted(TREE_CASES))
+def test_tree_invariants(api, case):
+    make, leaf = TREE_CASES[case]
+    pts = make()
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=leaf)
+    exp = tree.export()
+    st = check_tree(pts, exp, leaf_size=leaf, depth_cap=48)
+    assert exp["depth"] == st["depth"]
+    if case == "all_equal":
+        assert st["leaves"] == 1
+    if case == "depth_cap_chain":
+        assert st["depth"] == 48
+    tree.free()
+
+
+def test_empty_tree(api):
+    tree = api.pg_tree_build(torch.zeros((0, 3), device="cuda"), leaf_size=16)
+    q = _cuda(synth.uniform(10, 3, 1))
+    idx, dist = api.pg_knn(tree, q, 4)
+    assert torch.all(idx == -1) and torch.all(torch.isinf(dist))
+
+
+def test_all_knn_2d_20k_k5_full(api):
+    """2D all-kNN: n = 20,000 uniform points, leaf 16, k = 5, self included;
+    every row checked against the oracle."""
+    pts = synth.uniform(20000, 2, synth.BASE_SEED)
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
+    idx, dist = api.pg_knn(tree, None, 5)
+    o_idx, o_dist = oracle.knn(pts, pts, 5, nthreads=0)
+    compare_knn(idx.cpu().numpy(), dist.cpu().numpy(), o_idx, o_dist, pts, pts)
+    # self first (no duplicates in this set)
+    assert np.array_equal(idx[:, 0].cpu().numpy(), np.arange(20000))
+
+
+QUERY_CASES = [
+    (1, 3, "uniform"), (2, 1, "uniform"), (2, 7, "gmm"), (3, 10, "uniform"), (3, 16, "gmm"),
+    (3, 64, "uniform"), (4, 2, "gmm"), (5, 16, "gmm"), (6, 5, "uniform"), (7, 16, "gmm"),
+    (8, 33, "uniform"), (10, 9, "gmm"), (16, 12, "uniform"), (16, 64, "gmm"), (3, 4, "gmm"),
+]
+
+
+@pytest.mark.parametrize("d,k,dist_name", QUERY_CASES)
+def test_knn_separate_queries(api, d, k, dist_name):
+    gen = synth.uniform if dist_name == "uniform" else synth.gmm
+    pts = gen(12000, d, 100 + d)
+    q = gen(1500, d, 200 + d)
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
+    idx, dist = api.pg_knn(tree, _cuda(q), k)
+    o_idx, o_dist = oracle.knn(pts, q, k, nthreads=0)
+    compare_knn(idx.cpu().numpy(), dist.cpu().numpy(), o_idx, o_dist, pts, q)
+
+
+def test_knn_lattice_exact(api):
+    """Integer lattice: all distances are exact in float32, so the answer must
+    equal the oracle's bit for bit, ties broken by the smaller index."""
+    pts = synth.lattice((24, 20, 16))
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=8)
+    idx, dist = api.pg_knn(tree, None, 11)
+    o_idx, o_dist = oracle.knn(pts, pts, 11, nthreads=0)
+    assert np.array_equal(idx.cpu().numpy(), o_idx)
+    assert np.array_equal(dist.cpu().numpy().astype(np.float64), o_dist)
+
+
+def test_knn_duplicates_prefer_small_ids(api):
+    base = synth.uniform(300, 3, 21)
+    pts = np.concatenate([base] * 6)              # 6 copies, ids i, i+300, ...
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=4)
+    idx, dist = api.pg_knn(tree, _cuda(base), 6)
+    want = np.arange(300)[:, None] + 300 * np.arange(6)[None, :]
+    assert np.array_equal(idx.cpu().numpy(), want)
+    assert torch.all(dist == 0)
+
+
+def test_knn_padding(api):
+    pts = synth.uniform(3, 3, 22)
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
+    idx, dist = api.pg_knn(tree, _cuda(synth.uniform(5, 3, 23)), 10)
+    idx = idx.cpu().numpy()
+    assert np.all(idx[:, 3:] == -1) and torch.all(torch.isinf(dist[:, 3:]))
+    assert np.all(np.sort(idx[:, :3], axis=1) == np.arange(3))
+
+
+def test_knn_deterministic_and_stream(api):
+    pts = synth.gmm(50000, 3, 31)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        t1 = api.pg_tree_build(_cuda(pts), leaf_size=16)
+        a = api.pg_knn(t1, None, 10)
+        t2 = api.pg_tree_build(_cuda(pts), leaf_size=16)
+        b = api.pg_knn(t2, None, 10)
+    s.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    e1, e2 = t1.export(), t2.export()
+    assert np.array_equal(e1["nodes"].view(np.uint32), e2["nodes"].view(np.uint32))
+    assert np.array_equal(e1["bucket"].view(np.uint32), e2["bucket"].view(np.uint32))
+
+
+def _sample_rows(m, count, seed):
+    return np.sort(synth.pick_rows(m, min(count, m), seed))
+
+
+def test_all_knn_3d_10m_k10_sampled(api):
+    """3D all-kNN at full size (n = 10,000,000, k = 10) in the benchmark's
+    launch configuration; sampled rows against the oracle, properties on all."""
+    n = 10_000_000
+    pts = synth.uniform(n, 3, synth.BASE_SEED + 2)
+    x = _cuda(pts)
+    for leaf in (8, 16, 32):
+        tree = api.pg_tree_build(x, leaf_size=leaf)
+        idx, dist = api.pg_knn(tree, None, 10)
+        rows = _sample_rows(n, 400, leaf)
+        o_idx, o_dist = oracle.knn(pts, pts[rows], 10, nthreads=0)
+        compare_knn(idx[rows].cpu().numpy(), dist[rows].cpu().numpy(), o_idx, o_dist, pts, pts[rows])
+        d = dist
+        assert torch.all(d[:, 1:] >= d[:, :-1])
+        assert torch.all(d[:, 0] == 0)
+        assert torch.all((idx >= 0) & (idx < n))
+        tree.free()
+        del idx, dist
+
+
+@pytest.mark.parametrize("d", [5, 7])
+def test_gmm_2m_1m_queries_k16_sampled(api, d):
+    mix = synth.gmm_mixture(d, synth.BASE_SEED + 3)
+    pts = synth.gmm_sample(2_000_000, mix, synth.BASE_SEED + 30 + d)
+    q = synth.gmm_sample(1_000_000, mix, synth.BASE_SEED + 40 + d)
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
+    idx, dist = api.pg_knn(tree, _cuda(q), 16)
+    rows = _sample_rows(len(q), 300, d)
+    o_idx, o_dist = oracle.knn(pts, q[rows], 16, nthreads=0)
+    compare_knn(idx[rows].cpu().numpy(), dist[rows].cpu().numpy(), o_idx, o_dist, pts, q[rows])
+    assert torch.all(dist[:, 1:] >= dist[:, :-1])
