@@ -199,7 +199,7 @@ PG_API pg_status pg_bdl_free(pg_bdl *bdl);
  *   grad_queries[i]  = sum_j 2 g_ij (q_i - p_idx(i,j))            (m*dim)
  *   grad_data[t]     = -sum_{(i,j): idx_ij = t} 2 g_ij (q_i - p_t) (n*dim)
  * Distances are recomputed from the coordinates (float32).  Entries with
- * idx < 0 are skipped.  grad_data is summed per data point in ascending
+ * idx < 0 (padding) or idx >= n are skipped.  grad_data is summed per data point in ascending
  * (i, j) order after a stable sort by index, so the result is bitwise
  * deterministic.  All pointers are device memory; either gradient may be
  * NULL.  Outputs are overwritten (not accumulated).  Stream-ordered.

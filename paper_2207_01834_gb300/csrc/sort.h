@@ -1,0 +1,15 @@
+// Stable radix sort of (key, value) pairs (device memory, stream-ordered).
+#pragma once
+
+#include "common.cuh"
+
+namespace pg {
+
+// Sorts n pairs by the low `bits` bits of the key, stably.  keys/vals hold the
+// input (vals is ignored and the item index used instead when iota_vals);
+// tk/tv are temporaries of n entries.  The sorted arrays end in whichever pair
+// of buffers *out_keys/*out_vals point to.
+pg_status radix_sort_pairs(uint32_t *keys, uint32_t *vals, bool iota_vals, uint32_t *tk, uint32_t *tv, int64_t n,
+                           int bits, cudaStream_t s, uint32_t **out_keys, uint32_t **out_vals);
+
+}  // namespace pg
