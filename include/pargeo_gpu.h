@@ -208,6 +208,27 @@ PG_API pg_status pg_knn_backward(const float *data, int64_t n, const float *quer
                           int k, const int32_t *idx, const float *grad_dist, float *grad_queries,
                           float *grad_data, void *stream);
 
+/*
+ * pg_knn_backward_noalloc — the paper has no counterpart (library service).
+ * Same inputs, outputs and results as pg_knn_backward, computed without any
+ * device allocation, for callers that cannot let a library allocate GPU
+ * memory: applications that reserve all device memory for their own pool at
+ * start-up, processes under a hard memory cap, and loops that must not pay
+ * for or synchronise on an allocation.  It works in one statically sized
+ * __device__ array (about 25 MiB) that stays resident on every GPU that loads
+ * the library until the process exits, and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ * Limits: n <= 1,048,576 data points and m*k <= 1,048,576 (query, neighbour)
+ * pairs; larger requests return PG_EINVAL and launch nothing.
+ * All calls share the array: calls whose GPU work overlaps (for example on two
+ * streams at once) race and must be serialised by the caller.  The first call
+ * on a device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  Stream-ordered otherwise.
+ */
+PG_API pg_status pg_knn_backward_noalloc(const float *data, int64_t n, const float *queries, int64_t m,
+                                         int dim, int k, const int32_t *idx, const float *grad_dist,
+                                         float *grad_queries, float *grad_data, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched multi-cloud Chamfer path (not in the paper: many uneven point
  * clouds built and queried in one persistent launch over a work queue).

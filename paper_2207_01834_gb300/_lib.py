@@ -54,6 +54,7 @@ SIGNATURES = {
     "pg_bdl_slot_of": (_S, [_P, _P]),
     "pg_bdl_free": (_S, [_P]),
     "pg_knn_backward": (_S, [_P, _I64, _P, _I64, _I, _I, _P, _P, _P, _P, _P]),
+    "pg_knn_backward_noalloc": (_S, [_P, _I64, _P, _I64, _I, _I, _P, _P, _P, _P, _P]),
     "pg_batched_chamfer": (_S, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
     "pg_batched_chamfer_backward": (_S, [_P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
     "pg_last_error": (C.c_char_p, []),

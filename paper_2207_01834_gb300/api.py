@@ -17,7 +17,8 @@ from ._lib import PgError, TreeInfo, call
 
 __all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_knn", "pg_tree_free", "pg_tree_info",
            "pg_tree_export", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
-           "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_batched_chamfer",
+           "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_knn_backward_noalloc",
+           "pg_batched_chamfer",
            "pg_batched_chamfer_backward", "launch_count", "profile_enable", "profile_read", "version",
            "debug_fail_alloc_after"]
 
@@ -245,6 +246,23 @@ def pg_knn_backward(data: torch.Tensor, queries: torch.Tensor, idx: torch.Tensor
          _ptr(idx) if m else None, _ptr(grad_dist) if m else None, _ptr(gq) if gq is not None and m else None,
          _ptr(gp) if gp is not None and n else None, _stream(stream))
     return gq, gp
+
+
+def pg_knn_backward_noalloc(data: torch.Tensor, queries: torch.Tensor, idx: torch.Tensor,
+                            grad_dist: torch.Tensor, grad_queries: torch.Tensor, grad_data: torch.Tensor,
+                            stream=None):
+    """pg_knn_backward into caller-provided outputs, using only the library's
+    fixed device scratch (no allocation by the library)."""
+    data = _dev(data, torch.float32, "data", 2)
+    queries = _dev(queries, torch.float32, "queries", 2)
+    idx = _dev(idx, torch.int32, "idx", 2)
+    grad_dist = _dev(grad_dist, torch.float32, "grad_dist", 2)
+    n, dim = data.shape
+    m, k = idx.shape
+    call("pg_knn_backward_noalloc", _ptr(data) if n else None, n, _ptr(queries) if m else None, m, dim, k,
+         _ptr(idx) if m else None, _ptr(grad_dist) if m else None, _ptr(grad_queries), _ptr(grad_data),
+         _stream(stream))
+    return grad_queries, grad_data
 
 
 # ---------------------------------------------------------------- batched

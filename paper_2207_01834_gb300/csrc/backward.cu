@@ -127,6 +127,37 @@ pg_status knn_backward_run(const float *data, int64_t n, const float *queries, i
     return check_launch("knn backward");
 }
 
+// The same computation on caller-provided scratch (knn_backward_scratch_bytes
+// plus radix_ws_words ints after it): no allocation.
+pg_status knn_backward_run_ws(const float *data, int64_t n, const float *queries, int64_t m, int dim, int k,
+                              const int32_t *idx, const float *g, float *gq, float *gp, void *scratch,
+                              int *radix_ws, cudaStream_t s) {
+    if (gq && m > 0) {
+        k_bwd_queries<<<grid_of(m), BT, 0, s>>>(data, n, queries, m, dim, k, idx, g, gq);
+        count_launch();
+    }
+    if (gp && n > 0) {
+        const int64_t P = m * k;
+        uint32_t *keys = reinterpret_cast<uint32_t *>(scratch);
+        uint32_t *vals = keys + P, *tk = vals + P, *tv = tk + P;
+        int *lo = reinterpret_cast<int *>(tv + P), *hi = lo + n;
+        PG_CUDA(cudaMemsetAsync(lo, 0, sizeof(int) * (size_t)(2 * n), s));
+        uint32_t *sk = keys, *sv = vals;
+        if (P > 0) {
+            k_bwd_keys<<<grid_of(P), BT, 0, s>>>(idx, P, (uint32_t)n, keys);
+            count_launch();
+            int bits = 1;
+            while (bits < 32 && ((uint64_t)1 << bits) <= (uint64_t)n) ++bits;
+            PG_TRY(radix_sort_pairs_ws(keys, vals, true, tk, tv, P, bits, radix_ws, s, &sk, &sv));
+            k_bwd_bounds<<<grid_of(P), BT, 0, s>>>(sk, P, (uint32_t)n, lo, hi);
+            count_launch();
+        }
+        k_bwd_data<<<grid_of(n), BT, 0, s>>>(data, queries, n, dim, k, sv, g, lo, hi, gp);
+        count_launch();
+    }
+    return check_launch("knn backward");
+}
+
 }  // namespace pg
 
 using namespace pg;

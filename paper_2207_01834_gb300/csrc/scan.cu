@@ -121,4 +121,23 @@ pg_status exclusive_scan(const int *in, int *out, int64_t n, cudaStream_t s) {
     return check_launch("exclusive_scan");
 }
 
+// Same scan with caller-provided partial-sum workspace (scan_ws_words(n) ints):
+// allocates nothing.
+int64_t scan_ws_words(int64_t n) { return n <= 0 ? 1 : (int64_t)ceil_div_i(n, kTile) + 1; }
+
+pg_status exclusive_scan_ws(const int *in, int *out, int64_t n, int *ws, cudaStream_t s) {
+    if (n <= 0) {
+        PG_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+        return PG_OK;
+    }
+    const int nb = ceil_div_i(n, kTile);
+    k_scan_reduce<<<nb, kThreads, 0, s>>>(in, n, ws);
+    count_launch();
+    k_scan_top<<<1, 1024, 0, s>>>(ws, nb);
+    count_launch();
+    k_scan_down<<<nb, kThreads, 0, s>>>(in, n, ws, nb, out);
+    count_launch();
+    return check_launch("exclusive_scan_ws");
+}
+
 }  // namespace pg

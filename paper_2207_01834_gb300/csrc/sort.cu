@@ -113,4 +113,38 @@ pg_status radix_sort_pairs(uint32_t *keys, uint32_t *vals, bool iota_vals, uint3
     return PG_OK;
 }
 
+int64_t radix_ws_words(int64_t n) {
+    const int64_t cells = (int64_t)kRadix * (n > 0 ? ceil_div_i(n, kTile) : 1);
+    return 2 * cells + 1 + scan_ws_words(cells);
+}
+
+pg_status radix_sort_pairs_ws(uint32_t *keys, uint32_t *vals, bool iota_vals, uint32_t *tk, uint32_t *tv,
+                              int64_t n, int bits, int *ws, cudaStream_t s, uint32_t **out_keys,
+                              uint32_t **out_vals) {
+    *out_keys = keys;
+    *out_vals = vals;
+    if (n <= 0) return PG_OK;
+    if (n >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "radix sort: too many items");
+    const int ntiles = ceil_div_i(n, kTile);
+    const int64_t cells = (int64_t)kRadix * ntiles;
+    int *hist = ws, *off = ws + cells, *scan_ws = off + cells + 1;
+    uint32_t *ik = keys, *iv = vals, *ok = tk, *ov = tv;
+    const int passes = bits <= 8 ? 1 : (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_rs_hist<<<ntiles, kThreads, 0, s>>>(ik, n, shift, ntiles, hist);
+        count_launch();
+        PG_TRY(exclusive_scan_ws(hist, off, cells, scan_ws, s));
+        k_rs_scatter<<<ntiles, kThreads, 0, s>>>(ik, (p == 0 && iota_vals) ? nullptr : iv, n, shift, ntiles, off,
+                                                 ok, ov);
+        count_launch();
+        PG_TRY(check_launch("radix sort"));
+        std::swap(ik, ok);
+        std::swap(iv, ov);
+    }
+    *out_keys = ik;
+    *out_vals = iv;
+    return PG_OK;
+}
+
 }  // namespace pg

@@ -12,4 +12,13 @@ namespace pg {
 pg_status radix_sort_pairs(uint32_t *keys, uint32_t *vals, bool iota_vals, uint32_t *tk, uint32_t *tv, int64_t n,
                            int bits, cudaStream_t s, uint32_t **out_keys, uint32_t **out_vals);
 
+// Workspace variants that allocate nothing: `ws` must hold radix_ws_words(n)
+// ints (scan_ws_words(n) for the scan).
+int64_t scan_ws_words(int64_t n);
+pg_status exclusive_scan_ws(const int *in, int *out, int64_t n, int *ws, cudaStream_t s);
+int64_t radix_ws_words(int64_t n);
+pg_status radix_sort_pairs_ws(uint32_t *keys, uint32_t *vals, bool iota_vals, uint32_t *tk, uint32_t *tv,
+                              int64_t n, int bits, int *ws, cudaStream_t s, uint32_t **out_keys,
+                              uint32_t **out_vals);
+
 }  // namespace pg
