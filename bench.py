@@ -44,9 +44,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--leaf", type=int, default=0, help="leaf size (0: autotuned)")
+    p.add_argument("--variant", type=int, default=0, help="traversal: 0 auto, 1 thread per query, 2 warp packets")
     p.add_argument("--n", type=int, default=N_POINTS, help=argparse.SUPPRESS)
     p.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -157,6 +159,64 @@ def cpu_baseline(pts, k, budget_s=12.0):
             "sample": f"{m} all-kNN queries (k={k}) against all {n} points, float64 brute force"}
 
 
+def batched_vs_plain(api, torch, dev, k: int, reps: int = 3):
+    """Batched fwd+bwd (one persistent launch + backward twin) vs the plain
+    per-cloud sequence (pg_tree_build + pg_knn per cloud and direction, then
+    pg_knn_backward per direction) on 256 cloud pairs of 1e3..1e5 points."""
+    from paper_2207_01834_gb300 import synth
+
+    a, a_off, b, b_off = synth.cloud_pairs(256, seed=synth.BASE_SEED + 5)
+    A = torch.from_numpy(a).to(dev)
+    B = torch.from_numpy(b).to(dev)
+    g = torch.ones(256, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        loss, iab, iba, _, _ = api.pg_batched_chamfer(A, a_off, B, b_off, k)
+        ga, gb = api.pg_batched_chamfer_backward(A, a_off, B, b_off, k, iab, iba, g)
+        return loss, iab, iba, ga, gb
+
+    def plain():
+        out = []
+        for i in range(256):
+            Ai = A[a_off[i]:a_off[i + 1]]
+            Bi = B[b_off[i]:b_off[i + 1]]
+            ta = api.pg_tree_build(Ai, 16)
+            tb = api.pg_tree_build(Bi, 16)
+            iab, dab = api.pg_knn(tb, Ai, k)
+            iba, dba = api.pg_knn(ta, Bi, k)
+            loss = dab.sum() + dba.sum()
+            w_ab = torch.ones_like(dab)
+            w_ba = torch.ones_like(dba)
+            ga1, gb1 = api.pg_knn_backward(Bi, Ai, iab, w_ab)
+            gb2, ga2 = api.pg_knn_backward(Ai, Bi, iba, w_ba)
+            out.append((loss, iab, iba, ga1 + ga2, gb1 + gb2))
+            ta.free()
+            tb.free()
+        return out
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best, r
+
+    tb_ms, rb = timed(batched)
+    tp_ms, rp = timed(plain)
+    same = bool(torch.equal(rb[1], torch.cat([x[1] for x in rp])) and
+                torch.equal(rb[2], torch.cat([x[2] for x in rp])))
+    return {"workload": "256 pairs of 3D clouds, sizes log-uniform [1e3, 1e5], 8-component GMM each",
+            "points": int(a_off[-1] + b_off[-1]), "k": k, "batched_fwd_bwd_ms": tb_ms,
+            "plain_fwd_bwd_ms": tp_ms, "speedup": tp_ms / tb_ms, "identical_indices": same}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -222,6 +282,7 @@ def run_ours(args):
     pts = synth.uniform(args.n, DIM, synth.BASE_SEED + 2)
     x = torch.from_numpy(pts).to(dev)
     n = len(pts)
+    api.pg_knn_set_variant(args.variant)
     leaf = args.leaf
     if leaf <= 0:
         from paper_2207_01834_gb300 import autotune
@@ -332,6 +393,8 @@ def run_ours(args):
             "build_ms": build_ms, "knn_ms": query_ms, "knn_mqps": n / (query_ms / 1e3) / 1e6,
             "roofline": roofline, "gpu_launches": launches, "e2e": e2e,
             "clocks": clk.summary()}
+    if rank == 0 and not args.no_batched:
+        line["batched_vs_plain"] = [batched_vs_plain(api, torch, dev, kk) for kk in (1, 8)]
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(pts, K)
     if rank == 0:

@@ -130,6 +130,17 @@ PG_API pg_status pg_tree_info(const pg_tree *tree, pg_tree_info_t *info);
 PG_API pg_status pg_tree_export(const pg_tree *tree, float *nodes, int32_t *split_dim, float *split_val,
                          float *bucket);
 
+/*
+ * Traversal variant used by pg_knn and pg_bdl_knn for every later call in this
+ * process (App. A.1.3 searches each query independently; both variants return
+ * that exact answer): 1 = one thread per query walks its own path; 2 = warp
+ * packets: the 32 queries of a warp, adjacent in tree order, share one walk
+ * and every lane scans every leaf any of them needs; 0 = automatic (currently
+ * one thread per query).  Separate queries are reordered by the leaf they fall
+ * in before a packet launch (m >= 4096).  Errors: PG_EINVAL for other values.
+ */
+PG_API pg_status pg_knn_set_variant(int variant);
+
 /* ------------------------------------------------------------------------
  * BDL-tree (paper Section 5; Appendix A.2 Insert_L, A.3 Erase_L, A.4 kNN_L).
  * A forest of static kd-trees in slots i = 0, 1, ... with capacity
@@ -244,7 +255,12 @@ PG_API pg_status pg_knn_backward_noalloc(const float *data, int64_t n, const flo
  *   idx_ba   (device, |b|*k int32)   neighbour rows local to A_i
  *   dist_ab / dist_ba (device float32, same shapes; may be NULL)
  * leaf_size as in pg_tree_build.  Each cloud must hold >= 1 point.
- * Stream-ordered (the plan is cached per (offsets, dim, k, leaf_size)).
+ * One persistent kernel builds every cloud's kd-tree and answers every query
+ * chunk from a work queue (builds first, largest first; a query chunk waits,
+ * bounded, for its two trees).  The plan (layout, queue, a CUDA graph of the
+ * launch sequence) is cached per (offsets, dim, k, leaf_size); each call
+ * replays the graph on `stream` and synchronises once to read the wait
+ * status.  Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT (a wait gave up).
  */
 PG_API pg_status pg_batched_chamfer(const float *a, const int64_t *a_off, const float *b,
                              const int64_t *b_off, int npairs, int dim, int k, int leaf_size,
@@ -288,6 +304,15 @@ PG_API pg_status pg_profile_read(const char *prefix, double *total_ms, int64_t *
 /* Fault injection for tests: the n-th device allocation from now fails with
  * PG_ENOMEM (n <= 0 disables).  Host-side only; no GPU fault is involved. */
 PG_API pg_status pg_debug_fail_alloc_after(int n);
+
+/*
+ * Fault injection for tests of the batched path's bounded waits: with
+ * skip_publish != 0 the build items never set their ready flags, so every
+ * query item waits until `wait_limit` spins (about 100 ns each; <= 0 restores
+ * the default of about two seconds) and pg_batched_chamfer returns
+ * PG_ETIMEOUT.  No GPU fault is involved.
+ */
+PG_API pg_status pg_debug_batched_faults(int skip_publish, long long wait_limit);
 
 #ifdef __cplusplus
 }

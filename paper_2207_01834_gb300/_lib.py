@@ -45,6 +45,7 @@ SIGNATURES = {
     "pg_tree_free": (_S, [_P]),
     "pg_tree_info": (_S, [_P, C.POINTER(TreeInfo)]),
     "pg_tree_export": (_S, [_P, _P, _P, _P, _P]),
+    "pg_knn_set_variant": (_S, [_I]),
     "pg_bdl_create": (_S, [_I, _I64, _I, _P, C.POINTER(_P)]),
     "pg_bdl_insert": (_S, [_P, _P, _I64, _P]),
     "pg_bdl_erase": (_S, [_P, _P, _I64]),
@@ -63,6 +64,7 @@ SIGNATURES = {
     "pg_profile_enable": (_S, [_I]),
     "pg_profile_read": (_S, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(_I64)]),
     "pg_debug_fail_alloc_after": (_S, [_I]),
+    "pg_debug_batched_faults": (_S, [_I, C.c_longlong]),
 }
 
 _lock = threading.Lock()

@@ -16,11 +16,11 @@ from . import _lib
 from ._lib import PgError, TreeInfo, call
 
 __all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_knn", "pg_tree_free", "pg_tree_info",
-           "pg_tree_export", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
+           "pg_tree_export", "pg_knn_set_variant", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
            "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_knn_backward_noalloc",
            "pg_batched_chamfer",
            "pg_batched_chamfer_backward", "launch_count", "profile_enable", "profile_read", "version",
-           "debug_fail_alloc_after"]
+           "debug_fail_alloc_after", "debug_batched_faults"]
 
 
 def _stream(stream=None) -> int:
@@ -130,6 +130,11 @@ def pg_tree_export(tree: Tree) -> dict:
             "root_lo": np.array(info.root_lo[:info.dim], np.float32),
             "root_hi": np.array(info.root_hi[:info.dim], np.float32), "num_nodes": nn,
             "depth": info.depth, "leaf_size": info.leaf_size}
+
+
+def pg_knn_set_variant(variant: int) -> None:
+    """0 automatic, 1 thread per query, 2 warp packets (process-wide)."""
+    call("pg_knn_set_variant", variant)
 
 
 # ---------------------------------------------------------------- BDL forest
@@ -326,3 +331,7 @@ def profile_read(prefix: str):
 
 def debug_fail_alloc_after(n: int) -> None:
     call("pg_debug_fail_alloc_after", n)
+
+
+def debug_batched_faults(skip_publish: bool, wait_limit: int = 0) -> None:
+    call("pg_debug_batched_faults", 1 if skip_publish else 0, wait_limit)

@@ -48,10 +48,19 @@ pg_status pg_knn(const pg_tree *tree, const float *queries, int64_t m, int k, in
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (tree->n == 0) {
         // Nothing to find: every slot is padding.
-        return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, m, tree->dim, k, out_idx, out_dist, s);
+        return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, nullptr, m, tree->dim, k, out_idx, out_dist, s);
     }
-    return knn_launch(tree->desc, 1, tree->dc, queries, queries ? nullptr : tree->bucket, m, tree->dim, k, out_idx,
-                      out_dist, s);
+    if (!queries)   // all-kNN: bucket order is already tree order
+        return knn_launch(tree->desc, 1, tree->dc, nullptr, tree->bucket, nullptr, m, tree->dim, k, out_idx,
+                          out_dist, s);
+    Scratch ord;
+    const bool sorted = knn_variant() != 1 && m >= kOrderMinQueries;
+    if (sorted) {
+        PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)m, s));
+        PG_TRY(query_order(tree, queries, m, tree->dim, ord.as<int32_t>(), s));
+    }
+    return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr, m, tree->dim,
+                      k, out_idx, out_dist, s);
 }
 
 pg_status pg_tree_free(pg_tree *tree) {

@@ -1,0 +1,410 @@
+// Host side of the batched multi-cloud Chamfer path: plan (layout, work queue,
+// scratch), a CUDA graph that replays {reset counters, persistent kernel,
+// per-pair loss sums} per call, and the deterministic backward twin.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "batched_kernel.cuh"
+#include "internal.h"
+#include "sort.h"
+
+namespace pg {
+
+#define PG_BDECL(DCN)                                                                                      \
+    pg_status batched_launch_dc##DCN(int, const BArgs *, const BWork *, int, int, int *, CloudMeta *, int *,  \
+                                     int *, float4 *, float4 *, float4 *, int *, float *, int2 *, int *,     \
+                                     float *, int, int, int, cudaStream_t);                                \
+    int batched_blocks_per_sm_dc##DCN(int k);
+PG_BDECL(2) PG_BDECL(3) PG_BDECL(4) PG_BDECL(5) PG_BDECL(6) PG_BDECL(7) PG_BDECL(8) PG_BDECL(12) PG_BDECL(16)
+#undef PG_BDECL
+
+namespace {
+
+constexpr int BT = 256;
+
+__global__ void k_pair_loss(const int *__restrict__ first, const float *__restrict__ partial, int npairs,
+                            float *__restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npairs) return;
+    float t = 0.f;
+    for (int x = first[i]; x < first[i + 1]; ++x) t += partial[x];
+    loss[i] = t;
+}
+
+// row -> pair index by binary search over the pair offsets
+__global__ void k_row_pair(const long long *__restrict__ off, int npairs, int64_t rows, int *__restrict__ pair) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    int lo = 0, hi = npairs;   // off[lo] <= r < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= r) lo = mid; else hi = mid;
+    }
+    pair[r] = lo;
+}
+
+// Sort keys of one direction: the global row of the neighbour in the other
+// array (or `sentinel` for padding).
+__global__ void k_bkeys(const int32_t *__restrict__ idx, int64_t rows, int k, const int *__restrict__ row_pair,
+                        const long long *__restrict__ other_off, uint32_t sentinel, uint32_t *__restrict__ keys) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= rows * k) return;
+    const int t = idx[p];
+    const int pr = row_pair[p / k];
+    const long long lim = other_off[pr + 1] - other_off[pr];
+    keys[p] = (t >= 0 && t < lim) ? (uint32_t)(other_off[pr] + t) : sentinel;
+}
+
+__global__ void k_bbounds(const uint32_t *__restrict__ sk, int64_t P, uint32_t n, int *__restrict__ lo,
+                          int *__restrict__ hi) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= P) return;
+    const uint32_t key = sk[x];
+    if (key >= n) return;
+    if (x == 0 || sk[x - 1] != key) lo[key] = (int)x;
+    if (x == P - 1 || sk[x + 1] != key) hi[key] = (int)(x + 1);
+}
+
+// Gradient of sum_i g_i loss_i for the rows of one array X (the other array
+// is Y):  direct part from X's own k neighbours in Y, then the contributions
+// of every Y row that selected this X row, in ascending (row, slot) order.
+__global__ void k_bgrad(const float *__restrict__ X, int64_t nx, const float *__restrict__ Y, int dim, int k,
+                        const int32_t *__restrict__ idx_xy, const int *__restrict__ row_pair_x,
+                        const int *__restrict__ row_pair_y, const long long *__restrict__ off_y,
+                        const float *__restrict__ g, const uint32_t *__restrict__ sv_yx, const int *__restrict__ lo,
+                        const int *__restrict__ hi, float *__restrict__ gx) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    float p[PG_MAX_DIM], acc[PG_MAX_DIM];
+#pragma unroll
+    for (int c = 0; c < PG_MAX_DIM; ++c) {
+        p[c] = c < dim ? X[x * dim + c] : 0.f;
+        acc[c] = 0.f;
+    }
+    const int pr = row_pair_x[x];
+    const float w = 2.f * g[pr];
+    const long long base = off_y[pr], lim = off_y[pr + 1] - base;
+    for (int j = 0; j < k; ++j) {
+        const int t = idx_xy[x * k + j];
+        if (t < 0 || t >= lim) continue;
+        const int64_t yr = base + t;
+#pragma unroll
+        for (int c = 0; c < PG_MAX_DIM; ++c)
+            if (c < dim) acc[c] = __fmaf_rn(w, __fsub_rn(p[c], Y[yr * dim + c]), acc[c]);
+    }
+    for (int e = lo[x]; e < hi[x]; ++e) {
+        const uint32_t v = sv_yx[e];
+        const int64_t yr = v / (uint32_t)k;
+        const float wy = -2.f * g[row_pair_y[yr]];
+#pragma unroll
+        for (int c = 0; c < PG_MAX_DIM; ++c)
+            if (c < dim) acc[c] = __fmaf_rn(wy, __fsub_rn(Y[yr * dim + c], p[c]), acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < PG_MAX_DIM; ++c)
+        if (c < dim) gx[x * dim + c] = acc[c];
+}
+
+inline int grid_of(int64_t n) { return std::max(1, ceil_div_i(n, BT)); }
+
+struct Plan {
+    int npairs = 0, dim = 0, k = 0, leaf = 0, dc = 2;
+    std::vector<long long> a_off, b_off;
+    int64_t Na = 0, Nb = 0, npoints = 0, nnodes = 0, nscratch = 0;
+    int nitems = 0, nbuild = 0, nquery = 0, grid = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // device
+    float4 *P = nullptr, *Q = nullptr, *nodes = nullptr;
+    int *sdim = nullptr, *scratch = nullptr, *ready = nullptr, *counter = nullptr, *status = nullptr;
+    float *sval = nullptr, *partial = nullptr;
+    int2 *range = nullptr;
+    CloudMeta *meta = nullptr;
+    BWork *items = nullptr;
+    BArgs *args = nullptr;
+    int *first = nullptr;
+    float *loss_dev = nullptr;
+    long long *aoff_d = nullptr, *boff_d = nullptr;
+    int *row_pair_a = nullptr, *row_pair_b = nullptr;
+    std::vector<void *> owned;
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (void *p : owned) cudaFree(p);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+long long g_wait_limit = kWaitLimit;
+int g_skip_publish = 0;
+
+std::mutex g_plans_mu;
+std::map<std::vector<long long>, std::unique_ptr<Plan>> g_plans;
+
+template <class T>
+pg_status plan_alloc(Plan &pl, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "batched plan allocation");
+    pl.owned.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return PG_OK;
+}
+
+int blocks_per_sm(int dc, int k) {
+    switch (dc) {
+        case 2: return batched_blocks_per_sm_dc2(k);
+        case 3: return batched_blocks_per_sm_dc3(k);
+        case 4: return batched_blocks_per_sm_dc4(k);
+        case 5: return batched_blocks_per_sm_dc5(k);
+        case 6: return batched_blocks_per_sm_dc6(k);
+        case 7: return batched_blocks_per_sm_dc7(k);
+        case 8: return batched_blocks_per_sm_dc8(k);
+        case 12: return batched_blocks_per_sm_dc12(k);
+        default: return batched_blocks_per_sm_dc16(k);
+    }
+}
+
+pg_status launch_kernel(Plan &pl, cudaStream_t s) {
+#define PG_BL(D)                                                                                           \
+    case D:                                                                                                \
+        return batched_launch_dc##D(pl.grid, pl.args, pl.items, pl.nitems, pl.nbuild, pl.counter, pl.meta,  \
+                                    pl.ready, pl.status, pl.P, pl.Q, pl.nodes, pl.sdim, pl.sval, pl.range,  \
+                                    pl.scratch, pl.partial, pl.dim, pl.k, pl.leaf, s);
+    switch (pl.dc) {
+        PG_BL(2) PG_BL(3) PG_BL(4) PG_BL(5) PG_BL(6) PG_BL(7) PG_BL(8) PG_BL(12) PG_BL(16)
+        default: return fail(PG_EUNSUPPORTED, "dimension class");
+    }
+#undef PG_BL
+}
+
+// Enqueue one forward pass (everything inside the captured graph).
+pg_status enqueue_forward(Plan &pl, cudaStream_t s) {
+    PG_CUDA(cudaMemsetAsync(pl.ready, 0, sizeof(int) * (size_t)(2 * pl.npairs), s));
+    PG_CUDA(cudaMemsetAsync(pl.counter, 0, sizeof(int), s));
+    PG_CUDA(cudaMemsetAsync(pl.status, 0, sizeof(int), s));
+    PG_TRY(launch_kernel(pl, s));
+    k_pair_loss<<<grid_of(pl.npairs), BT, 0, s>>>(pl.first, pl.partial, pl.npairs, pl.loss_dev);
+    count_launch();
+    return check_launch("batched loss");
+}
+
+pg_status make_plan(Plan &pl) {
+    const int np = pl.npairs;
+    const int W = bucket_w(pl.dc), NWv = node_w(pl.dc);
+    (void)W;
+    (void)NWv;
+    std::vector<CloudMeta> meta(2 * np);
+    int64_t pos = 0, node = 0, scr = 0;
+    std::vector<std::pair<int, int>> order;   // (size, cloud)
+    for (int i = 0; i < np; ++i) {
+        for (int side = 0; side < 2; ++side) {
+            const int c = 2 * i + side;
+            const std::vector<long long> &off = side == 0 ? pl.a_off : pl.b_off;
+            const int64_t n = off[i + 1] - off[i];
+            CloudMeta &m = meta[c];
+            memset(&m, 0, sizeof(m));
+            m.off = (int)pos;
+            m.n = (int)n;
+            m.node_base = (int)node;
+            m.row0 = (int)off[i];
+            m.src = side;
+            m.scratch_off = scr;
+            // 8-entry alignment keeps every cloud's buckets and nodes on their
+            // own 128-byte lines (readers never see another cloud's stale line)
+            pos += (n + 7) / 8 * 8;
+            node += (std::max<int64_t>(n - 1, 1) + 7) / 8 * 8;
+            scr += (cta_scratch_words(n, pl.leaf, pl.dc) + 31) / 32 * 32;
+            order.push_back({(int)n, c});
+        }
+    }
+    if (pos >= ((int64_t)1 << 31) || node >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "batched: too many points");
+    pl.npoints = pos;
+    pl.nnodes = node;
+    pl.nscratch = scr;
+    std::sort(order.begin(), order.end(), [](auto &x, auto &y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
+    std::vector<BWork> items;
+    for (auto &o : order) items.push_back({0, o.second, 0, 0});
+    pl.nbuild = (int)items.size();
+    std::vector<int> first(np + 1, 0);
+    for (int i = 0; i < np; ++i) {
+        first[i] = (int)items.size() - pl.nbuild;
+        for (int dir = 0; dir < 2; ++dir) {
+            const int n = meta[2 * i + dir].n;
+            for (int st = 0; st < n; st += BATCH_NT) items.push_back({1, i, dir, st});
+        }
+    }
+    first[np] = (int)items.size() - pl.nbuild;
+    pl.nitems = (int)items.size();
+    pl.nquery = pl.nitems - pl.nbuild;
+    const int W4 = bucket_w(pl.dc);
+    PG_TRY(plan_alloc(pl, &pl.P, (size_t)pl.npoints * W4));
+    PG_TRY(plan_alloc(pl, &pl.Q, (size_t)pl.npoints * W4));
+    PG_TRY(plan_alloc(pl, &pl.nodes, (size_t)pl.nnodes * node_w(pl.dc)));
+    PG_TRY(plan_alloc(pl, &pl.sdim, (size_t)pl.nnodes));
+    PG_TRY(plan_alloc(pl, &pl.sval, (size_t)pl.nnodes));
+    PG_TRY(plan_alloc(pl, &pl.range, (size_t)pl.nnodes));
+    PG_TRY(plan_alloc(pl, &pl.scratch, (size_t)pl.nscratch));
+    PG_TRY(plan_alloc(pl, &pl.ready, (size_t)(2 * np)));
+    PG_TRY(plan_alloc(pl, &pl.counter, 1));
+    PG_TRY(plan_alloc(pl, &pl.status, 1));
+    PG_TRY(plan_alloc(pl, &pl.partial, (size_t)pl.nquery));
+    PG_TRY(plan_alloc(pl, &pl.meta, (size_t)(2 * np)));
+    PG_TRY(plan_alloc(pl, &pl.items, (size_t)pl.nitems));
+    PG_TRY(plan_alloc(pl, &pl.args, 1));
+    PG_TRY(plan_alloc(pl, &pl.first, (size_t)(np + 1)));
+    PG_TRY(plan_alloc(pl, &pl.loss_dev, (size_t)np));
+    PG_TRY(plan_alloc(pl, &pl.aoff_d, (size_t)(np + 1)));
+    PG_TRY(plan_alloc(pl, &pl.boff_d, (size_t)(np + 1)));
+    PG_CUDA(cudaMemcpy(pl.meta, meta.data(), sizeof(CloudMeta) * meta.size(), cudaMemcpyHostToDevice));
+    PG_CUDA(cudaMemcpy(pl.items, items.data(), sizeof(BWork) * items.size(), cudaMemcpyHostToDevice));
+    PG_CUDA(cudaMemcpy(pl.first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
+    PG_CUDA(cudaMemcpy(pl.aoff_d, pl.a_off.data(), sizeof(long long) * (np + 1), cudaMemcpyHostToDevice));
+    PG_CUDA(cudaMemcpy(pl.boff_d, pl.b_off.data(), sizeof(long long) * (np + 1), cudaMemcpyHostToDevice));
+    pl.grid = num_sms() * blocks_per_sm(pl.dc, pl.k);
+    // capture the forward sequence once; calls only refresh the argument block
+    PG_CUDA(cudaStreamCreateWithFlags(&pl.cap, cudaStreamNonBlocking));
+    PG_CUDA(cudaStreamBeginCapture(pl.cap, cudaStreamCaptureModeThreadLocal));
+    pg_status st = enqueue_forward(pl, pl.cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(pl.cap, &graph);
+    if (st != PG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return cuda_fail(e, "batched graph capture");
+    e = cudaGraphInstantiate(&pl.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batched graph instantiate");
+    return PG_OK;
+}
+
+pg_status get_plan(const int64_t *a_off, const int64_t *b_off, int npairs, int dim, int k, int leaf, Plan **out) {
+    std::vector<long long> key = {npairs, dim, k, leaf};
+    for (int i = 0; i <= npairs; ++i) key.push_back(a_off[i]);
+    for (int i = 0; i <= npairs; ++i) key.push_back(b_off[i]);
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) { *out = it->second.get(); return PG_OK; }
+    std::unique_ptr<Plan> pl(new Plan());
+    pl->npairs = npairs;
+    pl->dim = dim;
+    pl->k = k;
+    pl->leaf = leaf;
+    pl->dc = dim_class(dim);
+    pl->a_off.assign(a_off, a_off + npairs + 1);
+    pl->b_off.assign(b_off, b_off + npairs + 1);
+    pl->Na = a_off[npairs];
+    pl->Nb = b_off[npairs];
+    PG_TRY(make_plan(*pl));
+    if (g_plans.size() > 16) g_plans.clear();   // bound the cache
+    *out = pl.get();
+    g_plans[key] = std::move(pl);
+    return PG_OK;
+}
+
+pg_status check_offsets(const int64_t *off, int npairs, const char *what) {
+    if (off[0] != 0) return fail(PG_EINVAL, std::string("pg_batched_chamfer: ") + what + "[0] must be 0");
+    for (int i = 0; i < npairs; ++i)
+        if (off[i + 1] <= off[i]) return fail(PG_EINVAL, std::string("pg_batched_chamfer: every cloud needs >= 1 point (") + what + ")");
+    if (off[npairs] >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "pg_batched_chamfer: too many points");
+    return PG_OK;
+}
+
+}  // namespace
+
+}  // namespace pg
+
+using namespace pg;
+
+extern "C" pg_status pg_batched_chamfer(const float *a, const int64_t *a_off, const float *b, const int64_t *b_off,
+                                        int npairs, int dim, int k, int leaf_size, float *loss, int32_t *idx_ab,
+                                        int32_t *idx_ba, float *dist_ab, float *dist_ba, void *stream) {
+    if (npairs < 1) return fail(PG_EINVAL, "pg_batched_chamfer: npairs must be >= 1");
+    if (dim < 1 || dim > PG_MAX_DIM) return fail(PG_EINVAL, "pg_batched_chamfer: dim must be in [1, 16]");
+    if (k < 1 || k > PG_MAX_K) return fail(PG_EINVAL, "pg_batched_chamfer: k must be in [1, 64]");
+    if (leaf_size < 1 || leaf_size > PG_MAX_LEAF) return fail(PG_EINVAL, "pg_batched_chamfer: leaf_size must be in [1, 256]");
+    if (!a || !b || !a_off || !b_off || !loss || !idx_ab || !idx_ba) return fail(PG_EINVAL, "pg_batched_chamfer: NULL argument");
+    PG_TRY(check_offsets(a_off, npairs, "a_off"));
+    PG_TRY(check_offsets(b_off, npairs, "b_off"));
+    if ((a_off[npairs] + b_off[npairs]) * (int64_t)k >= ((int64_t)1 << 31))
+        return fail(PG_EINVAL, "pg_batched_chamfer: (|a| + |b|) * k must be < 2^31");
+    Plan *pl = nullptr;
+    PG_TRY(get_plan(a_off, b_off, npairs, dim, k, leaf_size, &pl));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BArgs args{a, b, idx_ab, idx_ba, dist_ab, dist_ba, g_wait_limit, g_skip_publish};
+    PG_CUDA(cudaMemcpyAsync(pl->args, &args, sizeof(args), cudaMemcpyHostToDevice, s));
+    PG_CUDA(cudaGraphLaunch(pl->exec, s));
+    count_launch();   // persistent kernel
+    count_launch();   // per-pair loss sums
+    PG_CUDA(cudaMemcpyAsync(loss, pl->loss_dev, sizeof(float) * npairs, cudaMemcpyDeviceToDevice, s));
+    int st = 0;
+    PG_CUDA(cudaMemcpyAsync(&st, pl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    if (st) return fail(PG_ETIMEOUT, "pg_batched_chamfer: a query waited too long for a tree");
+    return PG_OK;
+}
+
+extern "C" pg_status pg_debug_batched_faults(int skip_publish, long long wait_limit) {
+    g_skip_publish = skip_publish ? 1 : 0;
+    g_wait_limit = wait_limit > 0 ? wait_limit : kWaitLimit;
+    return PG_OK;
+}
+
+extern "C" pg_status pg_batched_chamfer_backward(const float *a, const int64_t *a_off, const float *b,
+                                                 const int64_t *b_off, int npairs, int dim, int k,
+                                                 const int32_t *idx_ab, const int32_t *idx_ba,
+                                                 const float *grad_loss, float *grad_a, float *grad_b,
+                                                 void *stream) {
+    if (npairs < 1) return fail(PG_EINVAL, "pg_batched_chamfer_backward: npairs must be >= 1");
+    if (dim < 1 || dim > PG_MAX_DIM) return fail(PG_EINVAL, "pg_batched_chamfer_backward: dim must be in [1, 16]");
+    if (k < 1 || k > PG_MAX_K) return fail(PG_EINVAL, "pg_batched_chamfer_backward: k must be in [1, 64]");
+    if (!a || !b || !a_off || !b_off || !idx_ab || !idx_ba || !grad_loss || !grad_a || !grad_b)
+        return fail(PG_EINVAL, "pg_batched_chamfer_backward: NULL argument");
+    PG_TRY(check_offsets(a_off, npairs, "a_off"));
+    PG_TRY(check_offsets(b_off, npairs, "b_off"));
+    const int64_t Na = a_off[npairs], Nb = b_off[npairs];
+    if ((Na + Nb) * (int64_t)k >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "pg_batched_chamfer_backward: too many pairs");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Scratch offs, rp, sc;
+    PG_TRY(offs.alloc(sizeof(long long) * 2 * (npairs + 1), s));
+    long long *aoff = offs.as<long long>(), *boff = aoff + npairs + 1;
+    PG_CUDA(cudaMemcpyAsync(aoff, a_off, sizeof(long long) * (npairs + 1), cudaMemcpyHostToDevice, s));
+    PG_CUDA(cudaMemcpyAsync(boff, b_off, sizeof(long long) * (npairs + 1), cudaMemcpyHostToDevice, s));
+    PG_TRY(rp.alloc(sizeof(int) * (size_t)(Na + Nb), s));
+    int *rpa = rp.as<int>(), *rpb = rpa + Na;
+    k_row_pair<<<grid_of(Na), BT, 0, s>>>(aoff, npairs, Na, rpa);
+    k_row_pair<<<grid_of(Nb), BT, 0, s>>>(boff, npairs, Nb, rpb);
+    count_launch();
+    count_launch();
+    const int64_t Pab = Na * k, Pba = Nb * k, Pm = std::max(Pab, Pba);
+    // keys, vals, two temporaries (for the larger direction) + bounds for a and b
+    PG_TRY(sc.alloc(sizeof(uint32_t) * (size_t)(4 * Pm) + sizeof(int) * (size_t)(2 * std::max(Na, Nb)) + 256, s));
+    uint32_t *keys = sc.as<uint32_t>(), *vals = keys + Pm, *tk = vals + Pm, *tv = tk + Pm;
+    int *lo = reinterpret_cast<int *>(tv + Pm), *hi = lo + std::max(Na, Nb);
+    auto bits_for = [](int64_t n) { int b = 1; while (b < 32 && ((int64_t)1 << b) <= n) ++b; return b; };
+    // grad_b: b rows' own neighbours in a (idx_ba) + a rows that selected them (idx_ab)
+    for (int side = 0; side < 2; ++side) {
+        const bool for_b = side == 0;
+        const int64_t nx = for_b ? Nb : Na, ny = for_b ? Na : Nb;
+        const int32_t *idx_yx = for_b ? idx_ab : idx_ba;    // Y rows selecting X rows
+        const int *rpy = for_b ? rpa : rpb;
+        const long long *offx = for_b ? boff : aoff;
+        const int64_t P = ny * k;
+        PG_CUDA(cudaMemsetAsync(lo, 0, sizeof(int) * (size_t)(2 * std::max(Na, Nb)), s));
+        k_bkeys<<<grid_of(P), BT, 0, s>>>(idx_yx, ny, k, rpy, offx, (uint32_t)nx, keys);
+        count_launch();
+        uint32_t *sk, *sv;
+        PG_TRY(radix_sort_pairs(keys, vals, true, tk, tv, P, bits_for(nx), s, &sk, &sv));
+        k_bbounds<<<grid_of(P), BT, 0, s>>>(sk, P, (uint32_t)nx, lo, lo + std::max(Na, Nb));
+        count_launch();
+        KTimer kt("batched_backward_grad", s);
+        k_bgrad<<<grid_of(nx), BT, 0, s>>>(for_b ? b : a, nx, for_b ? a : b, dim, k, for_b ? idx_ba : idx_ab,
+                                            for_b ? rpb : rpa, rpy, for_b ? aoff : boff, grad_loss, sv, lo,
+                                            lo + std::max(Na, Nb), for_b ? grad_b : grad_a);
+        count_launch();
+        PG_TRY(check_launch("batched backward"));
+    }
+    (void)hi;
+    return PG_OK;
+}

@@ -1,0 +1,5 @@
+// Batched persistent kernels for dimension class 8.
+#include "batched_kernel.cuh"
+#include "internal.h"
+
+PG_DEFINE_BATCHED_LAUNCH(8)

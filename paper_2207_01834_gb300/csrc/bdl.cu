@@ -468,7 +468,18 @@ pg_status pg_bdl_knn(const pg_bdl *b, const float *queries, int64_t m, int k, in
     if (m > 0 && (!queries || !out_idx || !out_dist)) return fail(PG_EINVAL, "pg_bdl_knn: NULL pointer");
     if (m == 0) return PG_OK;
     PG_TRY(refresh_forest(b));
-    return knn_launch(b->forest, b->forest_n, b->dc, queries, nullptr, m, b->dim, k, out_idx, out_dist, b->s);
+    // order the queries by the leaves of the largest tree
+    const pg_tree *big = nullptr;
+    for (int i = 0; i < 64; ++i)
+        if (b->slot[i] && b->slot[i]->live > 0 && (!big || b->slot[i]->live > big->live)) big = b->slot[i];
+    Scratch ord;
+    const bool sorted = big && knn_variant() != 1 && m >= kOrderMinQueries;
+    if (sorted) {
+        PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)m, b->s));
+        PG_TRY(query_order(big, queries, m, b->dim, ord.as<int32_t>(), b->s));
+    }
+    return knn_launch(b->forest, b->forest_n, b->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr, m, b->dim,
+                      k, out_idx, out_dist, b->s);
 }
 
 pg_status pg_bdl_size(const pg_bdl *b, int64_t *live) {

@@ -24,6 +24,7 @@ namespace pg {
 namespace {
 
 constexpr int BT = 256;
+constexpr int kSmemChildren = 64;   // children reduced in shared memory first
 
 __device__ __forceinline__ float *rec_of(float4 *nodes, int node, int dc) {
     return reinterpret_cast<float *>(nodes + (size_t)node * node_w(dc));
@@ -186,9 +187,23 @@ __global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restr
                                                 const int *__restrict__ split_flag,
                                                 const int *__restrict__ split_rank, const int *__restrict__ pre,
                                                 int *__restrict__ nx_start, int *__restrict__ nx_end,
-                                                int *__restrict__ nx_lo, int *__restrict__ nx_hi) {
+                                                int *__restrict__ nx_lo, int *__restrict__ nx_hi, int nchild) {
     constexpr int W = bucket_w(DC);
     const int lane = threadIdx.x & 31;
+    // With few children (top levels) every block first reduces the boxes in
+    // shared memory and then adds one global atomic per child and dimension;
+    // otherwise warps go straight to global memory.
+    __shared__ int s_lo[kSmemChildren * DC], s_hi[kSmemChildren * DC];
+    const bool use_smem = nchild <= kSmemChildren;
+    if (use_smem) {
+        for (int x = threadIdx.x; x < nchild * DC; x += blockDim.x) {
+            s_lo[x] = 0x7f800000;
+            s_hi[x] = (int)0x807fffffu;
+        }
+        __syncthreads();
+    }
+    int *box_lo = use_smem ? s_lo : nx_lo;
+    int *box_hi = use_smem ? s_hi : nx_hi;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -236,11 +251,18 @@ __global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restr
                 const int a = __reduce_min_sync(0xffffffffu, mine ? e : INT_MAX);
                 const int b = __reduce_max_sync(0xffffffffu, mine ? e : INT_MIN);
                 if (lane == leader) {
-                    atomicMin(&nx_lo[key * DC + d], a);
-                    atomicMax(&nx_hi[key * DC + d], b);
+                    atomicMin(&box_lo[key * DC + d], a);
+                    atomicMax(&box_hi[key * DC + d], b);
                 }
             }
             active &= ~grp;
+        }
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int x = threadIdx.x; x < nchild * DC; x += blockDim.x) {
+            if (s_lo[x] != 0x7f800000) atomicMin(&nx_lo[x], s_lo[x]);
+            if (s_hi[x] != (int)0x807fffffu) atomicMax(&nx_hi[x], s_hi[x]);
         }
     }
 }
@@ -363,7 +385,8 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         {
             KTimer kt("build_scatter", s);
             k_scatter<DC><<<grid_pts, BT, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
-                                                  split_rank, sPre.as<int>(), nxt.start, nxt.end, nxt.lo, nxt.hi);
+                                                  split_rank, sPre.as<int>(), nxt.start, nxt.end, nxt.lo, nxt.hi,
+                                                  2 * T);
             count_launch();
         }
         PG_TRY(check_launch("build scatter"));

@@ -52,9 +52,18 @@ TreeDesc tree_desc(const pg_tree *t);
 // k-NN over `ntrees` trees described in device memory.  If self_bucket is not
 // NULL the queries are the m bucket entries of that array and the output row
 // is the entry's id; otherwise queries are row-major m*dim floats.
+// order (may be NULL): processing order of the queries (a permutation of
+// 0..m-1 that puts queries of the same leaf next to each other).
 pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
-                     const float4 *self_bucket, int64_t m, int dim, int k, int32_t *out_idx,
-                     float *out_dist, cudaStream_t s);
+                     const float4 *self_bucket, const int32_t *order, int64_t m, int dim, int k,
+                     int32_t *out_idx, float *out_dist, cudaStream_t s);
 int k_class(int k);
+void set_knn_variant(int v);
+int knn_variant();
+
+// ---- order.cu
+// Queries sorted by the leaf of `t` they fall in (stable); order gets m ints.
+pg_status query_order(const pg_tree *t, const float *queries, int64_t m, int dim, int32_t *order, cudaStream_t s);
+constexpr int64_t kOrderMinQueries = 4096;
 
 }  // namespace pg

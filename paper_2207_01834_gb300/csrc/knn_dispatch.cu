@@ -4,8 +4,8 @@
 namespace pg {
 
 #define PG_DECL(DCN)                                                                                      \
-    pg_status knn_launch_dc##DCN(const TreeDesc *, int, const float *, const float4 *, int64_t, int, int, \
-                                 int32_t *, float *, cudaStream_t);
+    pg_status knn_launch_dc##DCN(const TreeDesc *, int, const float *, const float4 *, const int32_t *,     \
+                                 int64_t, int, int, int32_t *, float *, int, cudaStream_t);
 PG_DECL(2) PG_DECL(3) PG_DECL(4) PG_DECL(5) PG_DECL(6) PG_DECL(7) PG_DECL(8) PG_DECL(12) PG_DECL(16)
 #undef PG_DECL
 
@@ -20,22 +20,35 @@ int k_class(int k) {
     return 64;
 }
 
+static int g_variant = 0;   // 0 automatic, 1 thread per query, 2 warp packets
+
+void set_knn_variant(int v) { g_variant = v; }
+// automatic: thread per query (measured faster on 3D all-kNN so far)
+int knn_variant() { return g_variant == 2 ? 2 : 1; }
+
 pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
-                     const float4 *self_bucket, int64_t m, int dim, int k, int32_t *out_idx, float *out_dist,
-                     cudaStream_t s) {
+                     const float4 *self_bucket, const int32_t *order, int64_t m, int dim, int k, int32_t *out_idx,
+                     float *out_dist, cudaStream_t s) {
     if (m == 0) return PG_OK;
+    const int variant = knn_variant();
     switch (dc) {
-        case 2: return knn_launch_dc2(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
-        case 3: return knn_launch_dc3(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
-        case 4: return knn_launch_dc4(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
-        case 5: return knn_launch_dc5(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
-        case 6: return knn_launch_dc6(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
-        case 7: return knn_launch_dc7(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
-        case 8: return knn_launch_dc8(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
-        case 12: return knn_launch_dc12(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
-        case 16: return knn_launch_dc16(trees_dev, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist, s);
+        case 2: return knn_launch_dc2(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
+        case 3: return knn_launch_dc3(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
+        case 4: return knn_launch_dc4(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
+        case 5: return knn_launch_dc5(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
+        case 6: return knn_launch_dc6(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
+        case 7: return knn_launch_dc7(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
+        case 8: return knn_launch_dc8(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
+        case 12: return knn_launch_dc12(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
+        case 16: return knn_launch_dc16(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, s);
         default: return fail(PG_EUNSUPPORTED, "dimension class");
     }
 }
 
 }  // namespace pg
+
+extern "C" pg_status pg_knn_set_variant(int variant) {
+    if (variant < 0 || variant > 2) return pg::fail(PG_EINVAL, "pg_knn_set_variant: variant must be 0, 1 or 2");
+    pg::set_knn_variant(variant);
+    return PG_OK;
+}

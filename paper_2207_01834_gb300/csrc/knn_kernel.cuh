@@ -60,13 +60,20 @@ struct KList {
     }
 };
 
-template <int DC>
+// NC: read through the non-coherent read-only path (data constant for the
+// whole kernel); false for trees built earlier in the same kernel.
+template <bool NC>
+__device__ __forceinline__ float4 ld4(const float4 *p) { return NC ? __ldg(p) : *p; }
+template <bool NC>
+__device__ __forceinline__ float ld1(const float *p) { return NC ? __ldg(p) : *p; }
+
+template <int DC, bool NC = true>
 __device__ __forceinline__ void load_point(const float4 *__restrict__ bucket, int64_t i, float *p, unsigned &pid) {
     constexpr int W = bucket_w(DC);
     float v[4 * W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        float4 f = __ldg(bucket + i * W + w);
+        float4 f = ld4<NC>(bucket + i * W + w);
         v[4 * w] = f.x; v[4 * w + 1] = f.y; v[4 * w + 2] = f.z; v[4 * w + 3] = f.w;
     }
 #pragma unroll
@@ -144,6 +151,174 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packet traversal: the 32 queries of a warp, adjacent in tree order (bucket
+// order for all-kNN, leaf-sorted order for separate queries), share one walk
+// through the tree.  A child is entered when ANY lane still needs it (its box
+// is within that lane's k-th distance); every lane scans every entered leaf
+// against broadcast loads of the leaf's points.  Control flow is warp-uniform,
+// so no lane idles on divergence; lanes that did not need a leaf just fail
+// the k-th-distance test.  Each lane's k-list is still exact: a lane skips a
+// subtree only when its own box distance exceeds its own k-th distance.
+// The stack lives in registers spread over the lanes (entry e in lane e%32).
+constexpr int PKT_THREADS = 128;
+
+struct PktStack {
+    int ref0, ref1, cnt0, cnt1, box0, box1;   // box = 2*node + side, or -1 for a tree root
+    int sp;
+    __device__ __forceinline__ void push(int lane, int ref, int cnt, int box) {
+        if (sp < 2 * 32) {
+            if (lane == (sp & 31)) {
+                if (sp < 32) { ref0 = ref; cnt0 = cnt; box0 = box; }
+                else { ref1 = ref; cnt1 = cnt; box1 = box; }
+            }
+            ++sp;
+        }
+    }
+    __device__ __forceinline__ void pop(int &ref, int &cnt, int &box) {
+        --sp;
+        const int src = sp & 31;
+        const bool lo = sp < 32;
+        ref = __shfl_sync(0xffffffffu, lo ? ref0 : ref1, src);
+        cnt = __shfl_sync(0xffffffffu, lo ? cnt0 : cnt1, src);
+        box = __shfl_sync(0xffffffffu, lo ? box0 : box1, src);
+    }
+};
+
+template <int DC, int KC, bool NC = true>
+__device__ __forceinline__ void scan_leaf_packet(const float4 *__restrict__ bucket, int ref, int cnt,
+                                                 const float *q, KList<KC> &L) {
+#pragma unroll 2
+    for (int i = ref; i < ref + cnt; ++i) {
+        float p[DC];
+        unsigned pid;
+        load_point<DC, NC>(bucket, i, p, pid);
+        L.offer(sqdist<DC>(q, p), pid);
+    }
+}
+
+template <int DC, int KC, bool NC = true>
+__device__ __forceinline__ void search_tree_packet(const TreeDesc &T, const float *q, bool valid, int lane,
+                                                   KList<KC> &L) {
+    constexpr int NW = node_w(DC);
+    const int root_cnt = T.root_cnt;
+    if (root_cnt < 0) return;
+    float rlo[DC], rhi[DC];
+#pragma unroll
+    for (int c = 0; c < DC; ++c) { rlo[c] = T.root_lo[c]; rhi[c] = T.root_hi[c]; }
+    {
+        const float dr = boxdist<DC>(q, rlo, rhi);
+        if (!__any_sync(0xffffffffu, valid && dr <= L.kth())) return;
+    }
+    if (root_cnt > 0) {
+        scan_leaf_packet<DC, KC, NC>(T.bucket, T.root_ref, root_cnt, q, L);
+        return;
+    }
+    PktStack st;
+    st.sp = 0;
+    st.push(lane, T.root_ref, 0, -1);
+    while (st.sp > 0) {
+        int ref, cnt, box;
+        st.pop(ref, cnt, box);
+        float d;
+        if (box < 0) {
+            d = boxdist<DC>(q, rlo, rhi);
+        } else {
+            const float *rec = reinterpret_cast<const float *>(T.nodes + (size_t)(box >> 1) * NW);
+            float lo[DC], hi[DC];
+            const int off = (box & 1) * 2 * DC;
+#pragma unroll
+            for (int c = 0; c < DC; ++c) { lo[c] = ld1<NC>(rec + off + c); hi[c] = ld1<NC>(rec + off + DC + c); }
+            d = boxdist<DC>(q, lo, hi);
+        }
+        if (!__any_sync(0xffffffffu, valid && d <= L.kth())) continue;
+        if (cnt > 0) {
+            scan_leaf_packet<DC, KC, NC>(T.bucket, ref, cnt, q, L);
+            continue;
+        }
+        for (;;) {
+            float rec[4 * NW];
+            const float4 *np = T.nodes + (size_t)ref * NW;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                float4 f = ld4<NC>(np + w);
+                rec[4 * w] = f.x; rec[4 * w + 1] = f.y; rec[4 * w + 2] = f.z; rec[4 * w + 3] = f.w;
+            }
+            const int *ri = reinterpret_cast<const int *>(rec + 4 * DC);
+            const int r0 = ri[0], c0 = ri[1], r1 = ri[2], c1 = ri[3];
+            const float d0 = boxdist<DC>(q, rec, rec + DC);
+            const float d1 = boxdist<DC>(q, rec + 2 * DC, rec + 3 * DC);
+            const float kth = L.kth();
+            const bool n0 = valid && c0 >= 0 && d0 <= kth;
+            const bool n1 = valid && c1 >= 0 && d1 <= kth;
+            const unsigned b0 = __ballot_sync(0xffffffffu, n0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, n1);
+            if (!(b0 | b1)) break;
+            int first;
+            if (b0 && b1) {
+                // majority vote on which child is nearer among lanes that need it
+                const int v0 = __popc(__ballot_sync(0xffffffffu, n0 && (!n1 || d0 <= d1)));
+                const int v1 = __popc(__ballot_sync(0xffffffffu, n1 && (!n0 || d1 < d0)));
+                first = v0 >= v1 ? 0 : 1;
+                if (first == 0) st.push(lane, r1, c1, 2 * ref + 1);
+                else st.push(lane, r0, c0, 2 * ref);
+            } else {
+                first = b0 ? 0 : 1;
+            }
+            const int rf = first ? r1 : r0, cf = first ? c1 : c0;
+            if (cf > 0) {
+                scan_leaf_packet<DC, KC, NC>(T.bucket, rf, cf, q, L);
+                break;
+            }
+            ref = rf;
+        }
+    }
+}
+
+// Warp-coherent k-NN.  Processing position p = warp*32 + lane; with
+// self_bucket the query is bucket entry p (all-kNN); otherwise it is query
+// order[p] (or p when order is NULL).
+template <int DC, int KC>
+__global__ void __launch_bounds__(PKT_THREADS) k_knn_packet(const TreeDesc *__restrict__ trees, int ntrees,
+                                                            const float *__restrict__ queries,
+                                                            const float4 *__restrict__ self_bucket,
+                                                            const int32_t *__restrict__ order, int64_t m, int dim,
+                                                            int k, int32_t *__restrict__ out_idx,
+                                                            float *__restrict__ out_dist) {
+    const int lane = threadIdx.x & 31;
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = pos < m;
+    float q[DC];
+    int64_t row = 0;
+#pragma unroll
+    for (int c = 0; c < DC; ++c) q[c] = 0.f;
+    if (valid) {
+        if (self_bucket) {
+            unsigned qid;
+            load_point<DC>(self_bucket, pos, q, qid);
+            row = (int64_t)qid;
+        } else {
+            row = order ? (int64_t)order[pos] : pos;
+#pragma unroll
+            for (int c = 0; c < DC; ++c) q[c] = c < dim ? queries[row * dim + c] : 0.f;
+        }
+    }
+    KList<KC> L;
+    L.init(k);
+    for (int t = 0; t < ntrees; ++t) search_tree_packet<DC, KC>(trees[t], q, valid, lane, L);
+    if (!valid) return;
+    int32_t *oi = out_idx + row * k;
+    float *od = out_dist + row * k;
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        if (j >= KC - k) {
+            const int o = j - (KC - k);
+            oi[o] = L.id[j] == DEAD_ID ? -1 : (int32_t)L.id[j];
+            od[o] = L.d[j];
+        }
+    }
+}
+
 // queries: row-major m*dim (NULL when self_bucket is given).
 // self_bucket: the tree's own bucket entries as queries (all-kNN); the
 // output row is then the entry's id.
@@ -182,23 +357,34 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
 
 }  // namespace pg
 
-// Host launcher for one dimension class: picks the list capacity KC >= k.
+// Host launcher for one dimension class: picks the list capacity KC >= k and
+// the traversal variant (1 = thread per query, otherwise warp packets).
+#define PG_KNN_CASE(DCN, KCN)                                                                              \
+    case KCN:                                                                                              \
+        if (variant == 1)                                                                                  \
+            k_knn<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(trees, ntrees, queries,      \
+                                                                               self_bucket, m, dim, k,     \
+                                                                               out_idx, out_dist);         \
+        else                                                                                               \
+            k_knn_packet<DCN, KCN><<<ceil_div_i(m, PKT_THREADS), PKT_THREADS, 0, s>>>(                     \
+                trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist);                 \
+        break;
+
 #define PG_DEFINE_KNN_LAUNCH(DCN)                                                                          \
     namespace pg {                                                                                         \
     pg_status knn_launch_dc##DCN(const TreeDesc *trees, int ntrees, const float *queries,                  \
-                                 const float4 *self_bucket, int64_t m, int dim, int k, int32_t *out_idx,    \
-                                 float *out_dist, cudaStream_t s) {                                         \
-        const int grid = ceil_div_i(m, KNN_THREADS);                                                       \
+                                 const float4 *self_bucket, const int32_t *order, int64_t m, int dim,      \
+                                 int k, int32_t *out_idx, float *out_dist, int variant, cudaStream_t s) {  \
         KTimer kt("knn_traverse", s);                                                                      \
         switch (k_class(k)) {                                                                              \
-            case 1: k_knn<DCN, 1><<<grid, KNN_THREADS, 0, s>>>(trees, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist); break; \
-            case 2: k_knn<DCN, 2><<<grid, KNN_THREADS, 0, s>>>(trees, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist); break; \
-            case 4: k_knn<DCN, 4><<<grid, KNN_THREADS, 0, s>>>(trees, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist); break; \
-            case 8: k_knn<DCN, 8><<<grid, KNN_THREADS, 0, s>>>(trees, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist); break; \
-            case 10: k_knn<DCN, 10><<<grid, KNN_THREADS, 0, s>>>(trees, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist); break; \
-            case 16: k_knn<DCN, 16><<<grid, KNN_THREADS, 0, s>>>(trees, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist); break; \
-            case 32: k_knn<DCN, 32><<<grid, KNN_THREADS, 0, s>>>(trees, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist); break; \
-            case 64: k_knn<DCN, 64><<<grid, KNN_THREADS, 0, s>>>(trees, ntrees, queries, self_bucket, m, dim, k, out_idx, out_dist); break; \
+            PG_KNN_CASE(DCN, 1)                                                                            \
+            PG_KNN_CASE(DCN, 2)                                                                            \
+            PG_KNN_CASE(DCN, 4)                                                                            \
+            PG_KNN_CASE(DCN, 8)                                                                            \
+            PG_KNN_CASE(DCN, 10)                                                                           \
+            PG_KNN_CASE(DCN, 16)                                                                           \
+            PG_KNN_CASE(DCN, 32)                                                                           \
+            PG_KNN_CASE(DCN, 64)                                                                           \
             default: return fail(PG_EINVAL, "k out of range");                                             \
         }                                                                                                  \
         count_launch();                                                                                    \

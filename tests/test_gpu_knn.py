@@ -23,6 +23,13 @@ def api():
     return a
 
 
+@pytest.fixture(params=[1, 2], ids=["thread", "packet"])
+def variant(api, request):
+    api.pg_knn_set_variant(request.param)
+    yield request.param
+    api.pg_knn_set_variant(0)
+
+
 def _cuda(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
@@ -74,12 +81,15 @@ def test_empty_tree(api):
     assert torch.all(idx == -1) and torch.all(torch.isinf(dist))
 
 
-def test_all_knn_2d_20k_k5_full(api):
+def test_all_knn_2d_20k_k5_full(api, variant):
     """2D all-kNN: n = 20,000 uniform points, leaf 16, k = 5, self included;
     every row checked against the oracle."""
     pts = synth.uniform(20000, 2, synth.BASE_SEED)
     tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
     idx, dist = api.pg_knn(tree, None, 5)
+    # separate queries equal to the points take the leaf-ordered path
+    qi, qd = api.pg_knn(tree, _cuda(pts), 5)
+    assert torch.equal(qi, idx) and torch.equal(qd, dist)
     o_idx, o_dist = oracle.knn(pts, pts, 5, nthreads=0)
     compare_knn(idx.cpu().numpy(), dist.cpu().numpy(), o_idx, o_dist, pts, pts)
     # self first (no duplicates in this set)
@@ -94,7 +104,7 @@ QUERY_CASES = [
 
 
 @pytest.mark.parametrize("d,k,dist_name", QUERY_CASES)
-def test_knn_separate_queries(api, d, k, dist_name):
+def test_knn_separate_queries(api, variant, d, k, dist_name):
     gen = synth.uniform if dist_name == "uniform" else synth.gmm
     pts = gen(12000, d, 100 + d)
     q = gen(1500, d, 200 + d)
@@ -104,7 +114,7 @@ def test_knn_separate_queries(api, d, k, dist_name):
     compare_knn(idx.cpu().numpy(), dist.cpu().numpy(), o_idx, o_dist, pts, q)
 
 
-def test_knn_lattice_exact(api):
+def test_knn_lattice_exact(api, variant):
     """Integer lattice: all distances are exact in float32, so the answer must
     equal the oracle's bit for bit, ties broken by the smaller index."""
     pts = synth.lattice((24, 20, 16))
@@ -115,7 +125,7 @@ def test_knn_lattice_exact(api):
     assert np.array_equal(dist.cpu().numpy().astype(np.float64), o_dist)
 
 
-def test_knn_duplicates_prefer_small_ids(api):
+def test_knn_duplicates_prefer_small_ids(api, variant):
     base = synth.uniform(300, 3, 21)
     pts = np.concatenate([base] * 6)              # 6 copies, ids i, i+300, ...
     tree = api.pg_tree_build(_cuda(pts), leaf_size=4)
@@ -125,13 +135,28 @@ def test_knn_duplicates_prefer_small_ids(api):
     assert torch.all(dist == 0)
 
 
-def test_knn_padding(api):
+def test_knn_padding(api, variant):
     pts = synth.uniform(3, 3, 22)
     tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
     idx, dist = api.pg_knn(tree, _cuda(synth.uniform(5, 3, 23)), 10)
     idx = idx.cpu().numpy()
     assert np.all(idx[:, 3:] == -1) and torch.all(torch.isinf(dist[:, 3:]))
     assert np.all(np.sort(idx[:, :3], axis=1) == np.arange(3))
+
+
+def test_variants_agree_bitwise(api):
+    """Both traversal variants return the exact k smallest (float32 distance,
+    id) pairs, so their outputs are identical."""
+    pts = synth.gmm(60000, 3, 41)
+    q = synth.gmm(20000, 3, 42)
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
+    outs = []
+    for v in (1, 2):
+        api.pg_knn_set_variant(v)
+        outs.append(api.pg_knn(tree, _cuda(q), 12) + api.pg_knn(tree, None, 7))
+    api.pg_knn_set_variant(0)
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
 
 
 def test_knn_deterministic_and_stream(api):
@@ -174,7 +199,7 @@ def test_all_knn_3d_10m_k10_sampled(api):
 
 
 @pytest.mark.parametrize("d", [5, 7])
-def test_gmm_2m_1m_queries_k16_sampled(api, d):
+def test_gmm_2m_1m_queries_k16_sampled(api, variant, d):
     mix = synth.gmm_mixture(d, synth.BASE_SEED + 3)
     pts = synth.gmm_sample(2_000_000, mix, synth.BASE_SEED + 30 + d)
     q = synth.gmm_sample(1_000_000, mix, synth.BASE_SEED + 40 + d)
