@@ -102,7 +102,7 @@ typedef struct {
     int32_t dim;         /* coordinate count of the input                      */
     int32_t dim_class;   /* DC: coordinates stored per point (>= dim, padded 0)*/
     int32_t leaf_size;
-    int32_t num_nodes;   /* internal nodes                                     */
+    int32_t num_nodes;   /* node slots (some may be unused: cnt fields -1)     */
     int32_t depth;       /* deepest leaf                                       */
     int32_t node_floats; /* 32-bit words per node record = 4*DC + 4            */
     int32_t point_floats;/* 32-bit words per bucket entry = 4*ceil((DC+1)/4)   */
@@ -132,12 +132,14 @@ PG_API pg_status pg_tree_export(const pg_tree *tree, float *nodes, int32_t *spli
 
 /*
  * Traversal variant used by pg_knn and pg_bdl_knn for every later call in this
- * process (App. A.1.3 searches each query independently; both variants return
- * that exact answer): 1 = one thread per query walks its own path; 2 = warp
- * packets: the 32 queries of a warp, adjacent in tree order, share one walk
- * and every lane scans every leaf any of them needs; 0 = automatic (currently
- * one thread per query).  Separate queries are reordered by the leaf they fall
- * in before a packet launch (m >= 4096).  Errors: PG_EINVAL for other values.
+ * process (App. A.1.3 searches each query independently; every variant returns
+ * that same exact answer): 1 = one thread per query walks its own path;
+ * 2 = warp packets: the 32 queries of a warp, adjacent in tree order, share one
+ * walk and every lane scans every leaf any of them needs; 3 = one thread per
+ * query with postponed leaves: lanes walk nodes until each holds a leaf, then
+ * scan their leaves together; 0 = automatic (currently 1).  Separate queries
+ * (m >= 4096) are first reordered by the leaf they fall in, so that a warp's
+ * queries are neighbours.  Errors: PG_EINVAL for other values.
  */
 PG_API pg_status pg_knn_set_variant(int variant);
 

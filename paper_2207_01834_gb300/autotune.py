@@ -1,4 +1,5 @@
-"""Autotuner for the k-NN path's launch parameters.
+"""Autotuner for the k-NN path's launch parameters (leaf size, traversal
+variant: thread per query, warp packets or postponed leaves).
 
 It times the candidates on the caller's own data (build + query through the C
 ABI, CUDA events, after a warm-up) and caches the winner in a JSON file keyed
@@ -19,6 +20,7 @@ from .build import OUT_DIR
 
 CACHE = os.path.join(OUT_DIR, "autotune.json")
 LEAF_CANDIDATES = (8, 16, 32)
+VARIANT_CANDIDATES = (1, 2, 3)   # thread per query, warp packets, postponed leaves
 _lock = threading.Lock()
 
 
@@ -57,18 +59,33 @@ def _time_leaf(x: torch.Tensor, queries, k: int, leaf: int, reps: int = 2) -> fl
     return best
 
 
-def best_leaf(x: torch.Tensor, k: int, queries=None, candidates=LEAF_CANDIDATES) -> int:
-    """Leaf size minimising build + query time for this data (cached)."""
+def best_config(x: torch.Tensor, k: int, queries=None, leaves=LEAF_CANDIDATES,
+                variants=VARIANT_CANDIDATES) -> tuple[int, int]:
+    """(leaf size, traversal variant) minimising build + query time for this
+    data (cached).  Leaves the chosen variant set process-wide."""
     n, dim = x.shape
-    key = _key(dim, k, n, "leaf" if queries is None else "leaf_q")
+    key = _key(dim, k, n, "all" if queries is None else "queries") + \
+        f"|L{','.join(map(str, leaves))}|V{','.join(map(str, variants))}"
     with _lock:
         cache = _load()
         if key in cache:
-            return int(cache[key]["leaf"])
-    times = {leaf: _time_leaf(x, queries, k, leaf) for leaf in candidates}
-    leaf = min(times, key=times.get)
+            leaf, var = int(cache[key]["leaf"]), int(cache[key]["variant"])
+            api.pg_knn_set_variant(var)
+            return leaf, var
+    times = {}
+    for var in variants:
+        api.pg_knn_set_variant(var)
+        for leaf in leaves:
+            times[(leaf, var)] = _time_leaf(x, queries, k, leaf)
+    leaf, var = min(times, key=times.get)
+    api.pg_knn_set_variant(var)
     with _lock:
         cache = _load()
-        cache[key] = {"leaf": leaf, "ms": times}
+        cache[key] = {"leaf": leaf, "variant": var, "ms": {f"{a}/{b}": t for (a, b), t in times.items()}}
         _store(cache)
-    return leaf
+    return leaf, var
+
+
+def best_leaf(x: torch.Tensor, k: int, queries=None, candidates=LEAF_CANDIDATES) -> int:
+    """Leaf size (and, as a side effect, traversal variant) for this data."""
+    return best_config(x, k, queries, leaves=candidates)[0]

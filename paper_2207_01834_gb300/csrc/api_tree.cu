@@ -54,7 +54,7 @@ pg_status pg_knn(const pg_tree *tree, const float *queries, int64_t m, int k, in
         return knn_launch(tree->desc, 1, tree->dc, nullptr, tree->bucket, nullptr, m, tree->dim, k, out_idx,
                           out_dist, s);
     Scratch ord;
-    const bool sorted = knn_variant() != 1 && m >= kOrderMinQueries;
+    const bool sorted = m >= kOrderMinQueries;
     if (sorted) {
         PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)m, s));
         PG_TRY(query_order(tree, queries, m, tree->dim, ord.as<int32_t>(), s));

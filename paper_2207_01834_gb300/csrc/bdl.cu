@@ -473,7 +473,7 @@ pg_status pg_bdl_knn(const pg_bdl *b, const float *queries, int64_t m, int k, in
     for (int i = 0; i < 64; ++i)
         if (b->slot[i] && b->slot[i]->live > 0 && (!big || b->slot[i]->live > big->live)) big = b->slot[i];
     Scratch ord;
-    const bool sorted = big && knn_variant() != 1 && m >= kOrderMinQueries;
+    const bool sorted = big && m >= kOrderMinQueries;
     if (sorted) {
         PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)m, b->s));
         PG_TRY(query_order(big, queries, m, b->dim, ord.as<int32_t>(), b->s));

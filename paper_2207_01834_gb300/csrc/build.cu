@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "cta_build.cuh"
 #include "internal.h"
 
 namespace pg {
@@ -25,6 +26,10 @@ namespace {
 
 constexpr int BT = 256;
 constexpr int kSmemChildren = 64;   // children reduced in shared memory first
+
+struct Segs {
+    int *start, *end, *parent, *side, *depth, *lo, *hi;
+};
 
 __device__ __forceinline__ float *rec_of(float4 *nodes, int node, int dc) {
     return reinterpret_cast<float *>(nodes + (size_t)node * node_w(dc));
@@ -86,8 +91,9 @@ __global__ void __launch_bounds__(BT) k_pack(const float *__restrict__ src, cons
 template <int DC>
 __global__ void k_classify(int S, const int *__restrict__ start, const int *__restrict__ end,
                            const int *__restrict__ depth, const int *__restrict__ lo,
-                           const int *__restrict__ hi, int leaf, int depth_cap, int *__restrict__ split_flag,
-                           int *__restrict__ sdim, float *__restrict__ sval) {
+                           const int *__restrict__ hi, int leaf, int depth_cap, int fin_threshold,
+                           int *__restrict__ split_flag, int *__restrict__ fin_flag, int *__restrict__ sdim,
+                           float *__restrict__ sval) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     const int size = end[s] - start[s];
@@ -109,7 +115,10 @@ __global__ void k_classify(int S, const int *__restrict__ start, const int *__re
             bv = mid;
         }
     }
-    split_flag[s] = flag;
+    // a segment small enough for one block is finished by the block-scope builder
+    const int fin = flag && size <= fin_threshold;
+    split_flag[s] = flag && !fin;
+    fin_flag[s] = fin;
     sdim[s] = bd;
     sval[s] = bv;
 }
@@ -124,13 +133,38 @@ __global__ void k_link(int S, const int *__restrict__ start, const int *__restri
                        const int *__restrict__ sdim, const float *__restrict__ sval, int node_base,
                        float4 *__restrict__ nodes, int *__restrict__ n_sdim, float *__restrict__ n_sval,
                        int2 *__restrict__ n_range, int *__restrict__ nx_parent, int *__restrict__ nx_side,
-                       int *__restrict__ nx_depth, int *__restrict__ nx_lo, int *__restrict__ nx_hi) {
+                       int *__restrict__ nx_depth, int *__restrict__ nx_lo, int *__restrict__ nx_hi,
+                       const int *__restrict__ fin_flag, const int *__restrict__ fin_rank, int fin_base, Segs fin) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     const int st = start[s], size = end[s] - st;
     const int p = parent[s];
     const bool split = split_flag[s] != 0;
     const int node = node_base + split_rank[s];
+    if (fin_flag[s]) {
+        // handed to the block-scope builder, which links the subtree root
+        const int f = fin_base + fin_rank[s];
+        fin.start[f] = st;
+        fin.end[f] = st + size;
+        fin.parent[f] = p;
+        fin.side[f] = side[s];
+        fin.depth[f] = depth[s];
+#pragma unroll
+        for (int d = 0; d < DC; ++d) {
+            fin.lo[f * DC + d] = lo[s * DC + d];
+            fin.hi[f * DC + d] = hi[s * DC + d];
+        }
+        if (p >= 0) {
+            float *rec = rec_of(nodes, p, DC);
+            const int c = side[s];
+#pragma unroll
+            for (int d = 0; d < DC; ++d) {
+                rec[c * 2 * DC + d] = o2f(lo[s * DC + d]);
+                rec[c * 2 * DC + DC + d] = o2f(hi[s * DC + d]);
+            }
+        }
+        return;
+    }
     if (p >= 0) {
         float *rec = rec_of(nodes, p, DC);
         const int c = side[s];
@@ -267,9 +301,44 @@ __global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restr
     }
 }
 
-struct Segs {
-    int *start, *end, *parent, *side, *depth, *lo, *hi;
-};
+constexpr int FIN_NT = 256;
+constexpr int kFinThreshold = 16384;   // segments up to this size finish inside one block
+
+// Finisher scratch: segment f gets cta_scratch_words(n_f) ints at an offset
+// taken from an exclusive scan of the sizes in 32-int units (segments are
+// appended level by level, so their order is not bucket order).  Node slots
+// are reserved by bucket position: segment [st, en) may use [nb+st, nb+en).
+template <int DC>
+__global__ void k_fin_words(Segs fin, int count, int leaf, int *units) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < count) units[f] = (int)((cta_scratch_words(fin.end[f] - fin.start[f], leaf, DC) + 31) / 32);
+}
+
+template <int DC>
+__global__ void __launch_bounds__(FIN_NT) k_finish(Segs fin, float4 *P, float4 *Q, int *scratch,
+                                                   const int *__restrict__ unit_off, int leaf, int nb, float4 *nodes,
+                                                   int *n_sdim, float *n_sval, int2 *n_range, int *root_rec,
+                                                   int *depth_max) {
+    __shared__ int s_w[33];
+    const int f = blockIdx.x;
+    const int st = fin.start[f], en = fin.end[f];
+    const CtaTree r = cta_build_tree<DC, FIN_NT>(P, Q, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC,
+                                                 scratch + (long long)unit_off[f] * 32, leaf, nb + st,
+                                                 nodes, n_sdim, n_sval, n_range, s_w, fin.depth[f]);
+    if (threadIdx.x == 0) {
+        const int p = fin.parent[f];
+        if (p >= 0) {
+            int *ri = reinterpret_cast<int *>(nodes + (size_t)p * node_w(DC)) + 4 * DC;
+            const int c = fin.side[f];
+            ri[2 * c] = r.root_ref;
+            ri[2 * c + 1] = r.root_cnt;
+        } else {
+            root_rec[0] = r.root_ref;
+            root_rec[1] = r.root_cnt;
+        }
+        atomicMax(depth_max, r.depth);
+    }
+}
 
 template <int DC>
 struct Builder {
@@ -323,12 +392,25 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     const size_t seg_words = (size_t)seg_cap * (5 + 2 * DC);
     PG_TRY(sSegA.alloc(sizeof(int) * seg_words, s));
     PG_TRY(sSegB.alloc(sizeof(int) * seg_words, s));
-    // per-level: split_flag, split_rank (+1), sdim, sval
-    PG_TRY(sLvl.alloc(sizeof(int) * (size_t)(4 * seg_cap + 1), s));
+    // per-level: split_flag, split_rank (+1), sdim, sval, fin_flag, fin_rank (+1)
+    PG_TRY(sLvl.alloc(sizeof(int) * (size_t)(6 * seg_cap + 2), s));
     int *split_flag = sLvl.as<int>();
     int *split_rank = split_flag + seg_cap;
     int *sdim = split_rank + seg_cap + 1;
     float *sval = reinterpret_cast<float *>(sdim + seg_cap);
+    int *fin_flag = sdim + 2 * seg_cap;
+    int *fin_rank = fin_flag + seg_cap;
+    // segments handed to the block-scope finisher (disjoint, > leaf points each)
+    const int fin_cap = (int)(n / (leaf + 1) + 1);
+    Scratch sFin;
+    PG_TRY(sFin.alloc(sizeof(int) * (size_t)fin_cap * (5 + 2 * DC), s));
+    Segs fin;
+    {
+        int *b = sFin.as<int>();
+        fin.start = b; fin.end = b + fin_cap; fin.parent = b + 2 * fin_cap; fin.side = b + 3 * fin_cap;
+        fin.depth = b + 4 * fin_cap; fin.lo = b + 5 * fin_cap; fin.hi = b + (5 + DC) * fin_cap;
+    }
+    int fin_total = 0;
 
     auto carve = [&](Scratch &sc) {
         int *b = sc.as<int>();
@@ -354,7 +436,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         PG_CUDA(cudaMemcpyAsync(cur.lo, box, sizeof(int) * DC, cudaMemcpyDeviceToDevice, s));
         PG_CUDA(cudaMemcpyAsync(cur.hi, box + DC, sizeof(int) * DC, cudaMemcpyDeviceToDevice, s));
     }
-    int hT[1] = {0};
+    int hT[2] = {0, 0};
 
     int S = 1;
     int level = 0;
@@ -362,22 +444,26 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     bool root_split = false;
     t->num_nodes = 0;
     for (;;) {
+        if (level > PG_DEPTH_CAP + 1) return fail(PG_ECUDA, "tree build: level count exceeded the depth cap");
         const int gs = ceil_div_i(S, BT);
         k_classify<DC><<<gs, BT, 0, s>>>(S, cur.start, cur.end, cur.depth, cur.lo, cur.hi, leaf, PG_DEPTH_CAP,
-                                         split_flag, sdim, sval);
+                                         kFinThreshold, split_flag, fin_flag, sdim, sval);
         count_launch();
         PG_TRY(exclusive_scan(split_flag, split_rank, S, s));
+        PG_TRY(exclusive_scan(fin_flag, fin_rank, S, s));
         PG_CUDA(cudaMemcpyAsync(hT, split_rank + S, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaMemcpyAsync(hT + 1, fin_rank + S, sizeof(int), cudaMemcpyDeviceToHost, s));
         PG_CUDA(cudaStreamSynchronize(s));
-        const int T = *hT;
+        const int T = hT[0];
         if (level == 0) root_split = T > 0;
         PG_TRY(grow_nodes(t, node_base + T, s));
         k_link<DC><<<gs, BT, 0, s>>>(S, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo, cur.hi,
                                      split_flag, split_rank, sdim, sval, node_base, t->nodes, t->split_dim,
                                      t->split_val, t->node_range, nxt.parent, nxt.side, nxt.depth, nxt.lo,
-                                     nxt.hi);
+                                     nxt.hi, fin_flag, fin_rank, fin_total, fin);
         count_launch();
         PG_TRY(check_launch("build level"));
+        fin_total += hT[1];
         if (T == 0) break;
         k_flag<DC><<<grid_pts, BT, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, sFlag.as<int>());
         count_launch();
@@ -401,6 +487,41 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     t->depth = level;
     t->root_ref = 0;
     t->root_cnt = root_split ? 0 : (int)n;
+    if (fin_total > 0) {
+        // every finisher segment reserves node slots [node_base + st, node_base + en)
+        const int nb = node_base;
+        PG_TRY(grow_nodes(t, nb + (int)n, s));
+        PG_CUDA(cudaMemsetAsync(t->nodes + (size_t)nb * node_w(DC), 0xff, sizeof(float4) * node_w(DC) * (size_t)n, s));
+        t->num_nodes = nb + (int)n;
+        Scratch sUnits, sOff, sScr, sRec;
+        PG_TRY(sUnits.alloc(sizeof(int) * (size_t)fin_total, s));
+        PG_TRY(sOff.alloc(sizeof(int) * (size_t)(fin_total + 1), s));
+        k_fin_words<DC><<<ceil_div_i(fin_total, BT), BT, 0, s>>>(fin, fin_total, leaf, sUnits.as<int>());
+        count_launch();
+        PG_TRY(exclusive_scan(sUnits.as<int>(), sOff.as<int>(), fin_total, s));
+        int units = 0;
+        PG_CUDA(cudaMemcpyAsync(&units, sOff.as<int>() + fin_total, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+        PG_TRY(sScr.alloc(sizeof(int) * 32 * (size_t)units, s));
+        PG_TRY(sRec.alloc(sizeof(int) * 3, s));
+        int *rec = sRec.as<int>();
+        PG_CUDA(cudaMemsetAsync(rec, 0, sizeof(int) * 3, s));
+        {
+            KTimer kt("build_finish", s);
+            k_finish<DC><<<fin_total, FIN_NT, 0, s>>>(fin, P, Q, sScr.as<int>(), sOff.as<int>(), leaf, nb, t->nodes,
+                                                       t->split_dim, t->split_val, t->node_range, rec, rec + 2);
+            count_launch();
+        }
+        PG_TRY(check_launch("build finish"));
+        int h[3];
+        PG_CUDA(cudaMemcpyAsync(h, rec, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+        t->depth = std::max(t->depth, h[2]);
+        if (!root_split) {   // the whole tree was one finisher segment
+            t->root_ref = h[0];
+            t->root_cnt = h[1];
+        }
+    }
     // The final array becomes the bucket; the other ping-pong buffer is freed.
     if (P == P0) {
         t->bucket = P0;

@@ -104,7 +104,9 @@ struct CtaTree {
     int root_ref, root_cnt, nodes, depth;
 };
 
-// Build a kd-tree over bucket entries P[s0, s1) (already packed, any order).
+// Build a kd-tree over bucket entries P[s0, s1) (already packed, any order)
+// whose root sits at depth depth0 of an enclosing tree (the depth cap counts
+// from the enclosing root).
 // Q is a ping-pong buffer addressed by the same positions.  Nodes are written
 // to node indices node_base .. node_base + (s1 - s0 - 2) (at most n-1 nodes).
 // root_lo/root_hi: the range's tight box as order-preserving ints.
@@ -113,7 +115,7 @@ struct CtaTree {
 template <int DC, int NT>
 __device__ CtaTree cta_build_tree(float4 *P, float4 *Q, int s0, int s1, const int *root_lo, const int *root_hi,
                                   int *scratch, int leaf, int node_base, float4 *nodes, int *n_sdim,
-                                  float *n_sval, int2 *n_range, int *s_w) {
+                                  float *n_sval, int2 *n_range, int *s_w, int depth0 = 0) {
     constexpr int W = bucket_w(DC);
     const int n = s1 - s0;
     CtaScratch<DC> sc;
@@ -122,7 +124,7 @@ __device__ CtaTree cta_build_tree(float4 *P, float4 *Q, int s0, int s1, const in
     int *seg_cur = sc.seg_a, *seg_nxt = sc.seg_b;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        cur.start[0] = s0; cur.end[0] = s1; cur.parent[0] = -1; cur.side[0] = 0; cur.depth[0] = 0;
+        cur.start[0] = s0; cur.end[0] = s1; cur.parent[0] = -1; cur.side[0] = 0; cur.depth[0] = depth0;
     }
     if (threadIdx.x < DC) {
         cur.lo[threadIdx.x] = root_lo[threadIdx.x];
@@ -135,7 +137,9 @@ __device__ CtaTree cta_build_tree(float4 *P, float4 *Q, int s0, int s1, const in
     CtaTree res;
     res.root_ref = 0;
     res.root_cnt = n;
-    for (;;) {
+    // depth grows by one per level and nothing splits at the depth cap, so at
+    // most PG_DEPTH_CAP + 1 levels run; the bound also holds on bad input
+    for (int guard = 0; guard <= PG_DEPTH_CAP + 1; ++guard) {
         // classify
         for (int s = threadIdx.x; s < S; s += NT) {
             const int size = cur.end[s] - cur.start[s];
@@ -297,7 +301,7 @@ __device__ CtaTree cta_build_tree(float4 *P, float4 *Q, int s0, int s1, const in
     }
     __syncthreads();
     res.nodes = used;
-    res.depth = level;
+    res.depth = depth0 + level;
     return res;
 }
 

@@ -20,11 +20,11 @@ int k_class(int k) {
     return 64;
 }
 
-static int g_variant = 0;   // 0 automatic, 1 thread per query, 2 warp packets
+static int g_variant = 0;   // 0 automatic, 1 thread per query, 2 warp packets, 3 postponed leaves
 
 void set_knn_variant(int v) { g_variant = v; }
 // automatic: thread per query (measured faster on 3D all-kNN so far)
-int knn_variant() { return g_variant == 2 ? 2 : 1; }
+int knn_variant() { return g_variant == 0 ? 1 : g_variant; }
 
 pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
                      const float4 *self_bucket, const int32_t *order, int64_t m, int dim, int k, int32_t *out_idx,
@@ -48,7 +48,7 @@ pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float 
 }  // namespace pg
 
 extern "C" pg_status pg_knn_set_variant(int variant) {
-    if (variant < 0 || variant > 2) return pg::fail(PG_EINVAL, "pg_knn_set_variant: variant must be 0, 1 or 2");
+    if (variant < 0 || variant > 3) return pg::fail(PG_EINVAL, "pg_knn_set_variant: variant must be 0..3");
     pg::set_knn_variant(variant);
     return PG_OK;
 }

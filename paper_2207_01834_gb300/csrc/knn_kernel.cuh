@@ -58,6 +58,24 @@ struct KList {
         }
         if (less(x, ix, d[0], id[0])) { d[0] = x; id[0] = ix; }
     }
+    // Branch-free insertion executed by every lane of a warp; only lanes with
+    // `ok` (and a pair that precedes the k-th) change their list.  Every
+    // comparison reads the old list, so they are independent of each other.
+    __device__ __forceinline__ void offer_pred(float x, unsigned ix, bool ok) {
+        ok = ok && less(x, ix, d[KC - 1], id[KC - 1]);
+        bool prev = ok;   // x precedes slot j (old value)
+#pragma unroll
+        for (int j = KC - 1; j > 0; --j) {
+            const bool shift = ok && less(x, ix, d[j - 1], id[j - 1]);
+            const bool here = prev && !shift;
+            const float nd = shift ? d[j - 1] : (here ? x : d[j]);
+            const unsigned ni = shift ? id[j - 1] : (here ? ix : id[j]);
+            d[j] = nd;
+            id[j] = ni;
+            prev = shift;
+        }
+        if (prev) { d[0] = x; id[0] = ix; }
+    }
 };
 
 // NC: read through the non-coherent read-only path (data constant for the
@@ -152,6 +170,154 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
 }
 
 // ---------------------------------------------------------------------------
+// Thread-per-query traversal with postponed leaves ("while-while"): every lane
+// walks nodes (one pop or node expansion per step) until it holds a leaf to
+// scan or is finished; only when every lane of the warp is in that state do
+// the lanes scan their leaves together, so leaf work, the bulk of the
+// instructions, runs with the warp converged.  Candidates of a leaf chunk are
+// first tested against the lane's k-th pair into a bit mask, and the
+// insertions then run converged (as many rounds as the busiest lane needs).
+// Each lane's pruning uses only its own k-th distance, so the answer is the
+// same exact k-NN as the other variants.
+template <int DC, int KC>
+__device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict__ bucket, int lref, int lcnt,
+                                                        const float *q, KList<KC> &L) {
+    const int maxc = __reduce_max_sync(0xffffffffu, lcnt);
+    for (int base = 0; base < maxc; base += 32) {
+        const int n = min(32, maxc - base);
+        unsigned mask = 0;
+        const float kd = L.d[KC - 1];
+        const unsigned ki = L.id[KC - 1];
+        for (int j = 0; j < n; ++j) {
+            if (base + j < lcnt) {
+                float p[DC];
+                unsigned pid;
+                load_point<DC>(bucket, lref + base + j, p, pid);
+                const float dd = sqdist<DC>(q, p);
+                mask |= (KList<KC>::less(dd, pid, kd, ki) ? 1u : 0u) << j;
+            }
+        }
+        const int rounds = __reduce_max_sync(0xffffffffu, __popc(mask));
+        for (int t = 0; t < rounds; ++t) {
+            const bool act = mask != 0;
+            const int j = act ? __ffs(mask) - 1 : 0;
+            mask &= mask - 1;
+            float p[DC];
+            unsigned pid;
+            load_point<DC>(bucket, act ? lref + base + j : lref, p, pid);
+            L.offer_pred(sqdist<DC>(q, p), pid, act);
+        }
+    }
+}
+
+template <int DC, int KC>
+__device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q, bool valid, KList<KC> &L) {
+    constexpr int NW = node_w(DC);
+    int s_ref[KNN_STACK], s_cnt[KNN_STACK];
+    float s_d[KNN_STACK];
+    int sp = 0, ref = -1, lref = 0, lcnt = 0;
+    bool done = !valid || T.root_cnt < 0;
+    if (!done) {
+        float rlo[DC], rhi[DC];
+#pragma unroll
+        for (int c = 0; c < DC; ++c) { rlo[c] = T.root_lo[c]; rhi[c] = T.root_hi[c]; }
+        const float dr = boxdist<DC>(q, rlo, rhi);
+        if (dr > L.kth()) done = true;
+        else if (T.root_cnt > 0) { lref = T.root_ref; lcnt = T.root_cnt; }
+        else ref = T.root_ref;
+    }
+    for (;;) {
+        // node phase: lanes without a pending leaf advance until they get one
+        for (;;) {
+            const bool need = !done && lcnt == 0;
+            if (!__any_sync(0xffffffffu, need)) break;
+            if (need) {
+                if (ref < 0) {
+                    if (sp == 0) {
+                        done = true;
+                    } else {
+                        --sp;
+                        if (s_d[sp] <= L.kth()) {
+                            if (s_cnt[sp] > 0) { lref = s_ref[sp]; lcnt = s_cnt[sp]; }
+                            else ref = s_ref[sp];
+                        }
+                    }
+                }
+                if (ref >= 0) {
+                    float rec[4 * NW];
+                    const float4 *np = T.nodes + (size_t)ref * NW;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        float4 f = __ldg(np + w);
+                        rec[4 * w] = f.x; rec[4 * w + 1] = f.y; rec[4 * w + 2] = f.z; rec[4 * w + 3] = f.w;
+                    }
+                    const int *ri = reinterpret_cast<const int *>(rec + 4 * DC);
+                    const int r0 = ri[0], c0 = ri[1], r1 = ri[2], c1 = ri[3];
+                    const float d0 = boxdist<DC>(q, rec, rec + DC);
+                    const float d1 = boxdist<DC>(q, rec + 2 * DC, rec + 3 * DC);
+                    const bool sw = d1 < d0;
+                    const float dn = sw ? d1 : d0, df = sw ? d0 : d1;
+                    const int rn = sw ? r1 : r0, cn = sw ? c1 : c0;
+                    const int rf = sw ? r0 : r1, cf = sw ? c0 : c1;
+                    const float kth = L.kth();
+                    if (cf >= 0 && df <= kth && sp < KNN_STACK) {
+                        s_ref[sp] = rf; s_cnt[sp] = cf; s_d[sp] = df; ++sp;
+                    }
+                    ref = -1;
+                    if (cn >= 0 && dn <= kth) {
+                        if (cn > 0) { lref = rn; lcnt = cn; }
+                        else ref = rn;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, lcnt > 0)) break;
+        // leaf phase, converged
+        scan_own_leaf_converged<DC, KC>(T.bucket, lref, lcnt, q, L);
+        lcnt = 0;
+    }
+}
+
+template <int DC, int KC>
+__global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restrict__ trees, int ntrees,
+                                                        const float *__restrict__ queries,
+                                                        const float4 *__restrict__ self_bucket,
+                                                        const int32_t *__restrict__ order, int64_t m, int dim, int k,
+                                                        int32_t *__restrict__ out_idx, float *__restrict__ out_dist) {
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = pos < m;
+    float q[DC];
+    int64_t row = 0;
+#pragma unroll
+    for (int c = 0; c < DC; ++c) q[c] = 0.f;
+    if (valid) {
+        if (self_bucket) {
+            unsigned qid;
+            load_point<DC>(self_bucket, pos, q, qid);
+            row = (int64_t)qid;
+        } else {
+            row = order ? (int64_t)order[pos] : pos;
+#pragma unroll
+            for (int c = 0; c < DC; ++c) q[c] = c < dim ? queries[row * dim + c] : 0.f;
+        }
+    }
+    KList<KC> L;
+    L.init(k);
+    for (int t = 0; t < ntrees; ++t) search_tree_ww<DC, KC>(trees[t], q, valid, L);
+    if (!valid) return;
+    int32_t *oi = out_idx + row * k;
+    float *od = out_dist + row * k;
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        if (j >= KC - k) {
+            const int o = j - (KC - k);
+            oi[o] = L.id[j] == DEAD_ID ? -1 : (int32_t)L.id[j];
+            od[o] = L.d[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Packet traversal: the 32 queries of a warp, adjacent in tree order (bucket
 // order for all-kNN, leaf-sorted order for separate queries), share one walk
 // through the tree.  A child is entered when ANY lane still needs it (its box
@@ -185,21 +351,55 @@ struct PktStack {
     }
 };
 
+// Scan bucket entries [ref, ref+cnt) for every lane of the warp, skipping the
+// entries in [skip0, skip1) (already offered by the warm start).  Entries are
+// taken 32 at a time: every lane first tests all of them against its current
+// k-th pair and records the ones that pass in a bit mask; the insertions then
+// run converged, as many rounds as the busiest lane needs, so a lane's
+// insertion never stalls the other 31.
 template <int DC, int KC, bool NC = true>
 __device__ __forceinline__ void scan_leaf_packet(const float4 *__restrict__ bucket, int ref, int cnt,
-                                                 const float *q, KList<KC> &L) {
-#pragma unroll 2
-    for (int i = ref; i < ref + cnt; ++i) {
-        float p[DC];
-        unsigned pid;
-        load_point<DC, NC>(bucket, i, p, pid);
-        L.offer(sqdist<DC>(q, p), pid);
+                                                 const float *q, KList<KC> &L, int skip0 = 0, int skip1 = 0) {
+    // the part not yet offered: up to two pieces around the contiguous window
+    int r0 = ref, r1 = ref + cnt, r2 = 0, r3 = 0;
+    if (skip1 > skip0 && skip0 < r1 && r0 < skip1) {
+        const int e = r1;
+        r1 = max(r0, min(r1, skip0));
+        r2 = max(skip1, r0);
+        r3 = e > skip1 ? e : r2;
+    }
+    for (int piece = 0; piece < 2; ++piece) {
+        const int lo = piece ? r2 : r0, hi = piece ? r3 : r1;
+    for (int base = lo; base < hi; base += 32) {
+        const int n = min(32, hi - base);
+        unsigned mask = 0;
+        const float kd = L.d[KC - 1];
+        const unsigned ki = L.id[KC - 1];
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            float p[DC];
+            unsigned pid;
+            load_point<DC, NC>(bucket, base + j, p, pid);
+            const float dd = sqdist<DC>(q, p);
+            mask |= (KList<KC>::less(dd, pid, kd, ki) ? 1u : 0u) << j;
+        }
+        const int rounds = __reduce_max_sync(0xffffffffu, __popc(mask));
+        for (int t = 0; t < rounds; ++t) {
+            const bool act = mask != 0;
+            const int j = act ? __ffs(mask) - 1 : 0;
+            mask &= mask - 1;
+            float p[DC];
+            unsigned pid;
+            load_point<DC, NC>(bucket, base + j, p, pid);
+            L.offer_pred(sqdist<DC>(q, p), pid, act);
+        }
+    }
     }
 }
 
 template <int DC, int KC, bool NC = true>
 __device__ __forceinline__ void search_tree_packet(const TreeDesc &T, const float *q, bool valid, int lane,
-                                                   KList<KC> &L) {
+                                                   KList<KC> &L, int skip0 = 0, int skip1 = 0) {
     constexpr int NW = node_w(DC);
     const int root_cnt = T.root_cnt;
     if (root_cnt < 0) return;
@@ -211,7 +411,7 @@ __device__ __forceinline__ void search_tree_packet(const TreeDesc &T, const floa
         if (!__any_sync(0xffffffffu, valid && dr <= L.kth())) return;
     }
     if (root_cnt > 0) {
-        scan_leaf_packet<DC, KC, NC>(T.bucket, T.root_ref, root_cnt, q, L);
+        scan_leaf_packet<DC, KC, NC>(T.bucket, T.root_ref, root_cnt, q, L, skip0, skip1);
         return;
     }
     PktStack st;
@@ -233,7 +433,7 @@ __device__ __forceinline__ void search_tree_packet(const TreeDesc &T, const floa
         }
         if (!__any_sync(0xffffffffu, valid && d <= L.kth())) continue;
         if (cnt > 0) {
-            scan_leaf_packet<DC, KC, NC>(T.bucket, ref, cnt, q, L);
+            scan_leaf_packet<DC, KC, NC>(T.bucket, ref, cnt, q, L, skip0, skip1);
             continue;
         }
         for (;;) {
@@ -267,7 +467,7 @@ __device__ __forceinline__ void search_tree_packet(const TreeDesc &T, const floa
             }
             const int rf = first ? r1 : r0, cf = first ? c1 : c0;
             if (cf > 0) {
-                scan_leaf_packet<DC, KC, NC>(T.bucket, rf, cf, q, L);
+                scan_leaf_packet<DC, KC, NC>(T.bucket, rf, cf, q, L, skip0, skip1);
                 break;
             }
             ref = rf;
@@ -305,7 +505,17 @@ __global__ void __launch_bounds__(PKT_THREADS) k_knn_packet(const TreeDesc *__re
     }
     KList<KC> L;
     L.init(k);
-    for (int t = 0; t < ntrees; ++t) search_tree_packet<DC, KC>(trees[t], q, valid, lane, L);
+    if (self_bucket) {
+        // warm start: the warp's own bucket window (its queries and their
+        // neighbours in tree order) gives every lane a close k-th distance
+        // before the search; the search then skips that window.
+        const int64_t w0 = pos - lane;
+        const int64_t wl = max((int64_t)0, w0 - 16), wh = min(m, w0 + 48);
+        scan_leaf_packet<DC, KC>(self_bucket, (int)wl, (int)(wh - wl), q, L);
+        search_tree_packet<DC, KC>(trees[0], q, valid, lane, L, (int)wl, (int)wh);
+    } else {
+        for (int t = 0; t < ntrees; ++t) search_tree_packet<DC, KC>(trees[t], q, valid, lane, L);
+    }
     if (!valid) return;
     int32_t *oi = out_idx + row * k;
     float *od = out_dist + row * k;
@@ -365,6 +575,9 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
             k_knn<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(trees, ntrees, queries,      \
                                                                                self_bucket, m, dim, k,     \
                                                                                out_idx, out_dist);         \
+        else if (variant == 3)                                                                             \
+            k_knn_ww<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(                         \
+                trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist);                 \
         else                                                                                               \
             k_knn_packet<DCN, KCN><<<ceil_div_i(m, PKT_THREADS), PKT_THREADS, 0, s>>>(                     \
                 trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist);                 \

@@ -23,7 +23,7 @@ def api():
     return a
 
 
-@pytest.fixture(params=[1, 2], ids=["thread", "packet"])
+@pytest.fixture(params=[1, 2, 3], ids=["thread", "packet", "postponed"])
 def variant(api, request):
     api.pg_knn_set_variant(request.param)
     yield request.param
@@ -151,12 +151,13 @@ def test_variants_agree_bitwise(api):
     q = synth.gmm(20000, 3, 42)
     tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
     outs = []
-    for v in (1, 2):
+    for v in (1, 2, 3):
         api.pg_knn_set_variant(v)
         outs.append(api.pg_knn(tree, _cuda(q), 12) + api.pg_knn(tree, None, 7))
     api.pg_knn_set_variant(0)
-    for a, b in zip(outs[0], outs[1]):
-        assert torch.equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert torch.equal(a, b)
 
 
 def test_knn_deterministic_and_stream(api):
