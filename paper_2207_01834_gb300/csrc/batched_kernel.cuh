@@ -171,10 +171,10 @@ __global__ void __launch_bounds__(BATCH_NT) k_batched(const BArgs *__restrict__ 
                     for (int j = 0; j < KC; ++j) {
                         if (j >= KC - k) {
                             const int o = j - (KC - k);
-                            const bool pad = L.id[j] == DEAD_ID;
-                            oi[o] = pad ? -1 : (int32_t)L.id[j];
-                            if (od) od[o] = L.d[j];
-                            if (!pad) part += L.d[j];
+                            const bool pad = L.idx(j) == DEAD_ID;
+                            oi[o] = pad ? -1 : (int32_t)L.idx(j);
+                            if (od) od[o] = L.dist(j);
+                            if (!pad) part += L.dist(j);
                         }
                     }
                 }

@@ -24,57 +24,57 @@ namespace pg {
 constexpr int KNN_THREADS = 128;
 constexpr int KNN_STACK = PG_DEPTH_CAP + 2;
 
+// A (distance, id) pair is one 64-bit key: distances are >= 0, so their
+// float bits order like unsigned integers, and (bits << 32 | id) orders
+// exactly like (distance, id) lexicographically.  NaN (erased entries) sorts
+// above +inf and is never taken.
+__device__ __forceinline__ unsigned long long pair_key(float d, unsigned id) {
+    return ((unsigned long long)__float_as_uint(d) << 32) | id;
+}
+constexpr unsigned long long PAD_KEY = (0x7f800000ull << 32) | 0xffffffffull;   // (+inf, no point)
+
 template <int KC>
 struct KList {
-    float d[KC];
-    unsigned id[KC];
+    unsigned long long key[KC];
 
-    // Slots below KC-k hold -inf sentinels that never move, so a list of
-    // compile-time capacity KC serves any runtime k <= KC.
+    // Slots below KC-k hold the key 0, which never moves (nothing precedes
+    // it), so a list of compile-time capacity KC serves any runtime k <= KC.
     __device__ __forceinline__ void init(int k) {
 #pragma unroll
-        for (int j = 0; j < KC; ++j) {
-            const bool sentinel = j < KC - k;
-            d[j] = sentinel ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000);
-            id[j] = DEAD_ID;
-        }
+        for (int j = 0; j < KC; ++j) key[j] = j < KC - k ? 0ull : PAD_KEY;
     }
-    __device__ __forceinline__ float kth() const { return d[KC - 1]; }
+    __device__ __forceinline__ float kth() const { return __uint_as_float((unsigned)(key[KC - 1] >> 32)); }
+    __device__ __forceinline__ unsigned long long kth_key() const { return key[KC - 1]; }
+    __device__ __forceinline__ float dist(int j) const { return __uint_as_float((unsigned)(key[j] >> 32)); }
+    __device__ __forceinline__ unsigned idx(int j) const { return (unsigned)key[j]; }
 
-    __device__ __forceinline__ static bool less(float a, unsigned ia, float b, unsigned ib) {
-        return a < b || (a == b && ia < ib);
-    }
     // Insert (x, ix) if it precedes the current k-th pair.
     __device__ __forceinline__ void offer(float x, unsigned ix) {
-        if (!less(x, ix, d[KC - 1], id[KC - 1])) return;
+        const unsigned long long kx = pair_key(x, ix);
+        if (!(kx < key[KC - 1])) return;
 #pragma unroll
         for (int j = KC - 1; j > 0; --j) {
-            const bool shift = less(x, ix, d[j - 1], id[j - 1]);
-            const bool here = !shift && less(x, ix, d[j], id[j]);
-            const float nd = shift ? d[j - 1] : (here ? x : d[j]);
-            const unsigned ni = shift ? id[j - 1] : (here ? ix : id[j]);
-            d[j] = nd;
-            id[j] = ni;
+            const bool shift = kx < key[j - 1];
+            const bool here = !shift && kx < key[j];
+            key[j] = shift ? key[j - 1] : (here ? kx : key[j]);
         }
-        if (less(x, ix, d[0], id[0])) { d[0] = x; id[0] = ix; }
+        if (kx < key[0]) key[0] = kx;
     }
     // Branch-free insertion executed by every lane of a warp; only lanes with
     // `ok` (and a pair that precedes the k-th) change their list.  Every
     // comparison reads the old list, so they are independent of each other.
     __device__ __forceinline__ void offer_pred(float x, unsigned ix, bool ok) {
-        ok = ok && less(x, ix, d[KC - 1], id[KC - 1]);
+        const unsigned long long kx = pair_key(x, ix);
+        ok = ok && kx < key[KC - 1];
         bool prev = ok;   // x precedes slot j (old value)
 #pragma unroll
         for (int j = KC - 1; j > 0; --j) {
-            const bool shift = ok && less(x, ix, d[j - 1], id[j - 1]);
+            const bool shift = ok && kx < key[j - 1];
             const bool here = prev && !shift;
-            const float nd = shift ? d[j - 1] : (here ? x : d[j]);
-            const unsigned ni = shift ? id[j - 1] : (here ? ix : id[j]);
-            d[j] = nd;
-            id[j] = ni;
+            key[j] = shift ? key[j - 1] : (here ? kx : key[j]);
             prev = shift;
         }
-        if (prev) { d[0] = x; id[0] = ix; }
+        if (prev) key[0] = kx;
     }
 };
 
@@ -186,15 +186,14 @@ __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict
     for (int base = 0; base < maxc; base += 32) {
         const int n = min(32, maxc - base);
         unsigned mask = 0;
-        const float kd = L.d[KC - 1];
-        const unsigned ki = L.id[KC - 1];
+        const unsigned long long kk = L.kth_key();
         for (int j = 0; j < n; ++j) {
             if (base + j < lcnt) {
                 float p[DC];
                 unsigned pid;
                 load_point<DC>(bucket, lref + base + j, p, pid);
                 const float dd = sqdist<DC>(q, p);
-                mask |= (KList<KC>::less(dd, pid, kd, ki) ? 1u : 0u) << j;
+                mask |= (pair_key(dd, pid) < kk ? 1u : 0u) << j;
             }
         }
         const int rounds = __reduce_max_sync(0xffffffffu, __popc(mask));
@@ -311,8 +310,8 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
     for (int j = 0; j < KC; ++j) {
         if (j >= KC - k) {
             const int o = j - (KC - k);
-            oi[o] = L.id[j] == DEAD_ID ? -1 : (int32_t)L.id[j];
-            od[o] = L.d[j];
+            oi[o] = L.idx(j) == DEAD_ID ? -1 : (int32_t)L.idx(j);
+            od[o] = L.dist(j);
         }
     }
 }
@@ -373,15 +372,14 @@ __device__ __forceinline__ void scan_leaf_packet(const float4 *__restrict__ buck
     for (int base = lo; base < hi; base += 32) {
         const int n = min(32, hi - base);
         unsigned mask = 0;
-        const float kd = L.d[KC - 1];
-        const unsigned ki = L.id[KC - 1];
+        const unsigned long long kk = L.kth_key();
 #pragma unroll 4
         for (int j = 0; j < n; ++j) {
             float p[DC];
             unsigned pid;
             load_point<DC, NC>(bucket, base + j, p, pid);
             const float dd = sqdist<DC>(q, p);
-            mask |= (KList<KC>::less(dd, pid, kd, ki) ? 1u : 0u) << j;
+            mask |= (pair_key(dd, pid) < kk ? 1u : 0u) << j;
         }
         const int rounds = __reduce_max_sync(0xffffffffu, __popc(mask));
         for (int t = 0; t < rounds; ++t) {
@@ -523,8 +521,8 @@ __global__ void __launch_bounds__(PKT_THREADS) k_knn_packet(const TreeDesc *__re
     for (int j = 0; j < KC; ++j) {
         if (j >= KC - k) {
             const int o = j - (KC - k);
-            oi[o] = L.id[j] == DEAD_ID ? -1 : (int32_t)L.id[j];
-            od[o] = L.d[j];
+            oi[o] = L.idx(j) == DEAD_ID ? -1 : (int32_t)L.idx(j);
+            od[o] = L.dist(j);
         }
     }
 }
@@ -559,8 +557,8 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
     for (int j = 0; j < KC; ++j) {
         if (j >= KC - k) {
             const int o = j - (KC - k);
-            oi[o] = L.id[j] == DEAD_ID ? -1 : (int32_t)L.id[j];
-            od[o] = L.d[j];
+            oi[o] = L.idx(j) == DEAD_ID ? -1 : (int32_t)L.idx(j);
+            od[o] = L.dist(j);
         }
     }
 }
