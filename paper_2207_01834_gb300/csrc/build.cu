@@ -134,7 +134,8 @@ __global__ void k_link(int S, const int *__restrict__ start, const int *__restri
                        float4 *__restrict__ nodes, int *__restrict__ n_sdim, float *__restrict__ n_sval,
                        int2 *__restrict__ n_range, int *__restrict__ nx_parent, int *__restrict__ nx_side,
                        int *__restrict__ nx_depth, int *__restrict__ nx_lo, int *__restrict__ nx_hi,
-                       const int *__restrict__ fin_flag, const int *__restrict__ fin_rank, int fin_base, Segs fin) {
+                       const int *__restrict__ fin_flag, const int *__restrict__ fin_rank, int fin_base, Segs fin,
+                       int *__restrict__ n_parent, int *__restrict__ leaf_parent) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     const int st = start[s], size = end[s] - st;
@@ -165,6 +166,8 @@ __global__ void k_link(int S, const int *__restrict__ start, const int *__restri
         }
         return;
     }
+    const int code = p >= 0 ? 2 * p + side[s] : -1;   // where this segment hangs
+    if (split) n_parent[node] = code;
     if (p >= 0) {
         float *rec = rec_of(nodes, p, DC);
         const int c = side[s];
@@ -301,7 +304,10 @@ __global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restr
     }
 }
 
-constexpr int FIN_NT = 256;
+#ifndef PG_FIN_NT
+#define PG_FIN_NT 256
+#endif
+constexpr int FIN_NT = PG_FIN_NT;   // threads of a finisher block
 constexpr int kFinThreshold = 16384;   // segments up to this size finish inside one block
 
 // Finisher scratch: segment f gets cta_scratch_words(n_f) ints at an offset
@@ -315,16 +321,18 @@ __global__ void k_fin_words(Segs fin, int count, int leaf, int *units) {
 }
 
 template <int DC>
-__global__ void __launch_bounds__(FIN_NT) k_finish(Segs fin, float4 *P, float4 *Q, int *scratch,
+__global__ void __launch_bounds__(FIN_NT, 1024 / FIN_NT) k_finish(Segs fin, float4 *P, float4 *Q, int *scratch,
                                                    const int *__restrict__ unit_off, int leaf, int nb, float4 *nodes,
                                                    int *n_sdim, float *n_sval, int2 *n_range, int *root_rec,
-                                                   int *depth_max) {
+                                                   int *depth_max, int *n_parent, int *leaf_parent) {
     __shared__ int s_w[33];
     const int f = blockIdx.x;
     const int st = fin.start[f], en = fin.end[f];
     const CtaTree r = cta_build_tree<DC, FIN_NT>(P, Q, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC,
                                                  scratch + (long long)unit_off[f] * 32, leaf, nb + st,
-                                                 nodes, n_sdim, n_sval, n_range, s_w, fin.depth[f]);
+                                                 nodes, n_sdim, n_sval, n_range, s_w, fin.depth[f], n_parent,
+                                                 nullptr,
+                                                 fin.parent[f] >= 0 ? 2 * fin.parent[f] + fin.side[f] : -1);
     if (threadIdx.x == 0) {
         const int p = fin.parent[f];
         if (p >= 0) {
@@ -340,6 +348,21 @@ __global__ void __launch_bounds__(FIN_NT) k_finish(Segs fin, float4 *P, float4 *
     }
 }
 
+// Every bucket entry records the code (2*node + side) of the leaf that holds
+// it: one thread per node slot fills its leaf children's ranges (unused
+// slots have cnt = -1; entries of a leaf root keep -1).
+template <int DC>
+__global__ void k_leaf_parents(const float4 *__restrict__ nodes, int num_nodes, int *__restrict__ leaf_parent) {
+    const int nd = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nd >= num_nodes) return;
+    const int *ri = reinterpret_cast<const int *>(nodes + (size_t)nd * node_w(DC)) + 4 * DC;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int ref = ri[2 * c], cnt = ri[2 * c + 1];
+        for (int i = 0; i < cnt; ++i) leaf_parent[ref + i] = 2 * nd + c;
+    }
+}
+
 template <int DC>
 struct Builder {
     static pg_status run(float4 *packed, int *box, int64_t n, int leaf, cudaStream_t s, pg_tree *t);
@@ -349,28 +372,36 @@ pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
     if (need <= t->node_cap) return PG_OK;
     int cap = std::max(need, std::max(16, t->node_cap * 2));
     const int nw = node_w(t->dc);
-    float4 *nodes;
-    int *sd;
-    float *sv;
-    int2 *rg;
-    PG_TRY(dalloc_n(&nodes, (size_t)cap * nw, s));
-    if (dalloc_n(&sd, cap, s) != PG_OK) { dfree(nodes, s); return PG_ENOMEM; }
-    if (dalloc_n(&sv, cap, s) != PG_OK) { dfree(nodes, s); dfree(sd, s); return PG_ENOMEM; }
-    if (dalloc_n(&rg, cap, s) != PG_OK) { dfree(nodes, s); dfree(sd, s); dfree(sv, s); return PG_ENOMEM; }
+    float4 *nodes = nullptr;
+    int *sd = nullptr, *par = nullptr;
+    float *sv = nullptr;
+    int2 *rg = nullptr;
+    pg_status st = dalloc_n(&nodes, (size_t)cap * nw, s);
+    if (st == PG_OK) st = dalloc_n(&sd, cap, s);
+    if (st == PG_OK) st = dalloc_n(&sv, cap, s);
+    if (st == PG_OK) st = dalloc_n(&rg, cap, s);
+    if (st == PG_OK) st = dalloc_n(&par, cap, s);
+    if (st != PG_OK) {
+        dfree(nodes, s); dfree(sd, s); dfree(sv, s); dfree(rg, s); dfree(par, s);
+        return st;
+    }
     if (t->num_nodes > 0) {
         PG_CUDA(cudaMemcpyAsync(nodes, t->nodes, sizeof(float4) * nw * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
         PG_CUDA(cudaMemcpyAsync(sd, t->split_dim, sizeof(int) * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
         PG_CUDA(cudaMemcpyAsync(sv, t->split_val, sizeof(float) * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
         PG_CUDA(cudaMemcpyAsync(rg, t->node_range, sizeof(int2) * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
+        PG_CUDA(cudaMemcpyAsync(par, t->parent, sizeof(int) * (size_t)t->num_nodes, cudaMemcpyDeviceToDevice, s));
     }
     dfree(t->nodes, s);
     dfree(t->split_dim, s);
     dfree(t->split_val, s);
     dfree(t->node_range, s);
+    dfree(t->parent, s);
     t->nodes = nodes;
     t->split_dim = sd;
     t->split_val = sv;
     t->node_range = rg;
+    t->parent = par;
     t->node_cap = cap;
     return PG_OK;
 }
@@ -424,6 +455,8 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     float4 *P = P0, *Q = sP1.as<float4>();
     int *seg_of = sSeg0.as<int>(), *seg_of_nx = sSeg1.as<int>();
     PG_CUDA(cudaMemsetAsync(seg_of, 0, sizeof(int) * (size_t)n, s));   // all in segment 0
+    if (!t->leaf_parent) PG_TRY(dalloc_n(&t->leaf_parent, (size_t)n, s));
+    PG_TRY(grow_nodes(t, 16, s));   // the parent array must exist for the first link
 
     // level 0: one segment covering everything, box reduced by k_pack
     {
@@ -460,7 +493,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         k_link<DC><<<gs, BT, 0, s>>>(S, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo, cur.hi,
                                      split_flag, split_rank, sdim, sval, node_base, t->nodes, t->split_dim,
                                      t->split_val, t->node_range, nxt.parent, nxt.side, nxt.depth, nxt.lo,
-                                     nxt.hi, fin_flag, fin_rank, fin_total, fin);
+                                     nxt.hi, fin_flag, fin_rank, fin_total, fin, t->parent, t->leaf_parent);
         count_launch();
         PG_TRY(check_launch("build level"));
         fin_total += hT[1];
@@ -509,7 +542,8 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         {
             KTimer kt("build_finish", s);
             k_finish<DC><<<fin_total, FIN_NT, 0, s>>>(fin, P, Q, sScr.as<int>(), sOff.as<int>(), leaf, nb, t->nodes,
-                                                       t->split_dim, t->split_val, t->node_range, rec, rec + 2);
+                                                       t->split_dim, t->split_val, t->node_range, rec, rec + 2,
+                                                       t->parent, t->leaf_parent);
             count_launch();
         }
         PG_TRY(check_launch("build finish"));
@@ -521,6 +555,11 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
             t->root_ref = h[0];
             t->root_cnt = h[1];
         }
+    }
+    PG_CUDA(cudaMemsetAsync(t->leaf_parent, 0xff, sizeof(int) * (size_t)n, s));
+    if (t->num_nodes > 0) {
+        k_leaf_parents<DC><<<ceil_div_i(t->num_nodes, BT), BT, 0, s>>>(t->nodes, t->num_nodes, t->leaf_parent);
+        count_launch();
     }
     // The final array becomes the bucket; the other ping-pong buffer is freed.
     if (P == P0) {
@@ -630,6 +669,8 @@ TreeDesc tree_desc(const pg_tree *t) {
     memset(&d, 0, sizeof(d));
     d.bucket = t->bucket;
     d.nodes = t->nodes;
+    d.parent = t->parent;
+    d.leaf_parent = t->leaf_parent;
     d.root_ref = t->root_ref;
     d.root_cnt = t->root_cnt;
     for (int c = 0; c < PG_MAX_DIM; ++c) { d.root_lo[c] = t->root_lo[c]; d.root_hi[c] = t->root_hi[c]; }
@@ -651,12 +692,16 @@ void tree_release(pg_tree *t) {
     dfree(t->split_dim, s);
     dfree(t->split_val, s);
     dfree(t->node_range, s);
+    dfree(t->parent, s);
+    dfree(t->leaf_parent, s);
     dfree(t->desc, s);
     t->bucket = nullptr;
     t->nodes = nullptr;
     t->split_dim = nullptr;
     t->split_val = nullptr;
     t->node_range = nullptr;
+    t->parent = nullptr;
+    t->leaf_parent = nullptr;
     t->desc = nullptr;
 }
 

@@ -96,6 +96,8 @@ constexpr unsigned DEAD_ID = 0xFFFFFFFFu;
 struct TreeDesc {
     const float4 *bucket;
     const float4 *nodes;
+    const int *parent;        // per node: 2*parent + side (-1 at the root); may be NULL
+    const int *leaf_parent;   // per bucket entry: code of its leaf; may be NULL
     int root_ref;
     int root_cnt;   // >0 leaf root, 0 internal root, <0 empty / dead
     float root_lo[PG_MAX_DIM];

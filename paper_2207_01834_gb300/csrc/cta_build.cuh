@@ -106,7 +106,9 @@ struct CtaTree {
 
 // Build a kd-tree over bucket entries P[s0, s1) (already packed, any order)
 // whose root sits at depth depth0 of an enclosing tree (the depth cap counts
-// from the enclosing root).
+// from the enclosing root).  When n_parent / leaf_parent are given, every new
+// node and bucket entry records the code (2*parent node + side) of where it
+// hangs; root_code is that code for the range's own root (-1: tree root).
 // Q is a ping-pong buffer addressed by the same positions.  Nodes are written
 // to node indices node_base .. node_base + (s1 - s0 - 2) (at most n-1 nodes).
 // root_lo/root_hi: the range's tight box as order-preserving ints.
@@ -115,7 +117,8 @@ struct CtaTree {
 template <int DC, int NT>
 __device__ CtaTree cta_build_tree(float4 *P, float4 *Q, int s0, int s1, const int *root_lo, const int *root_hi,
                                   int *scratch, int leaf, int node_base, float4 *nodes, int *n_sdim,
-                                  float *n_sval, int2 *n_range, int *s_w, int depth0 = 0) {
+                                  float *n_sval, int2 *n_range, int *s_w, int depth0 = 0,
+                                  int *n_parent = nullptr, int *leaf_parent = nullptr, int root_code = -1) {
     constexpr int W = bucket_w(DC);
     const int n = s1 - s0;
     CtaScratch<DC> sc;
@@ -173,6 +176,13 @@ __device__ CtaTree cta_build_tree(float4 *P, float4 *Q, int s0, int s1, const in
             const bool split = sc.split[s] != 0;
             const int node = node_base + used + sc.rank[s];
             const int p = cur.parent[s];
+            // where this segment hangs in the whole tree (parent node, side)
+            const int code = p >= 0 ? 2 * p + cur.side[s] : root_code;
+            if (split) {
+                if (n_parent) n_parent[node] = code;
+            } else if (leaf_parent) {
+                for (int i = st; i < st + size; ++i) leaf_parent[i] = code;
+            }
             if (p >= 0) {
                 float *rec = reinterpret_cast<float *>(nodes + (size_t)p * node_w(DC));
                 const int c = cur.side[s];

@@ -23,6 +23,8 @@ struct pg_tree {
     int *split_dim = nullptr;    // node_cap
     float *split_val = nullptr;  // node_cap
     int2 *node_range = nullptr;  // node_cap: bucket range [x, y) of the node
+    int *parent = nullptr;       // node_cap: 2*parent_node + side, or -1 at the root
+    int *leaf_parent = nullptr;  // n: the code of the leaf holding each bucket entry
     pg::TreeDesc *desc = nullptr;  // device copy of this tree's descriptor
     cudaStream_t stream = nullptr;
     int64_t live = 0;            // live points (BDL trees lose points on erase)

@@ -48,17 +48,20 @@ struct KList {
     __device__ __forceinline__ float dist(int j) const { return __uint_as_float((unsigned)(key[j] >> 32)); }
     __device__ __forceinline__ unsigned idx(int j) const { return (unsigned)key[j]; }
 
-    // Insert (x, ix) if it precedes the current k-th pair.
+    // Insert (x, ix) if it precedes the current k-th pair.  Slot j takes slot
+    // j-1 while the new key precedes it, else the new key once; each
+    // comparison is made once and reused for the slot above.
     __device__ __forceinline__ void offer(float x, unsigned ix) {
         const unsigned long long kx = pair_key(x, ix);
         if (!(kx < key[KC - 1])) return;
+        bool prev = true;
 #pragma unroll
         for (int j = KC - 1; j > 0; --j) {
             const bool shift = kx < key[j - 1];
-            const bool here = !shift && kx < key[j];
-            key[j] = shift ? key[j - 1] : (here ? kx : key[j]);
+            key[j] = shift ? key[j - 1] : (prev ? kx : key[j]);
+            prev = shift;
         }
-        if (kx < key[0]) key[0] = kx;
+        if (prev) key[0] = kx;
     }
     // Branch-free insertion executed by every lane of a warp; only lanes with
     // `ok` (and a pair that precedes the k-th) change their list.  Every
@@ -106,7 +109,8 @@ __device__ __forceinline__ void scan_leaf(const float4 *__restrict__ bucket, int
         float p[DC];
         unsigned pid;
         load_point<DC>(bucket, i, p, pid);
-        L.offer(sqdist<DC>(q, p), pid);
+        const float d = sqdist<DC>(q, p);
+        if (d <= L.kth()) L.offer(d, pid);   // cheap float test rejects most candidates
     }
 }
 
@@ -527,6 +531,89 @@ __global__ void __launch_bounds__(PKT_THREADS) k_knn_packet(const TreeDesc *__re
     }
 }
 
+// All-kNN from the bottom: a query that is itself bucket entry `pos` starts in
+// its own leaf (which gives it a close k-th distance at once), then walks up
+// the parent links; at every ancestor only the other child's subtree can hold
+// points not seen yet, and it is searched top-down when its box is within the
+// k-th distance.  Every point lies in the own leaf or in exactly one such
+// sibling subtree, so the answer is the same exact k-NN, without the
+// top-down descent from the root.
+template <int DC, int KC>
+__device__ __forceinline__ void search_self_up(const TreeDesc &T, int64_t pos, const float *q, KList<KC> &L) {
+    constexpr int NW = node_w(DC);
+    int code = __ldg(T.leaf_parent + pos);
+    {
+        int lref, lcnt;
+        if (code < 0) { lref = T.root_ref; lcnt = T.root_cnt; }
+        else {
+            const int2 rc = __ldg(reinterpret_cast<const int2 *>(reinterpret_cast<const float *>(T.nodes + (size_t)(code >> 1) * NW) + 4 * DC) + (code & 1));
+            lref = rc.x;
+            lcnt = rc.y;
+        }
+        scan_leaf<DC, KC>(T.bucket, lref, lcnt, q, L);
+    }
+    int s_ref[KNN_STACK], s_cnt[KNN_STACK];
+    float s_d[KNN_STACK];
+    while (code >= 0) {
+        const int pn = code >> 1, other = 1 - (code & 1);
+        const float *rec = reinterpret_cast<const float *>(T.nodes + (size_t)pn * NW);
+        float lo[DC], hi[DC];
+#pragma unroll
+        for (int c = 0; c < DC; ++c) { lo[c] = __ldg(rec + other * 2 * DC + c); hi[c] = __ldg(rec + other * 2 * DC + DC + c); }
+        const int2 rc = __ldg(reinterpret_cast<const int2 *>(rec + 4 * DC) + other);
+        code = __ldg(T.parent + pn);
+        const float ds = boxdist<DC>(q, lo, hi);
+        if (rc.y < 0 || ds > L.kth()) continue;
+        if (rc.y > 0) {
+            scan_leaf<DC, KC>(T.bucket, rc.x, rc.y, q, L);
+            continue;
+        }
+        // top-down search of the sibling subtree
+        int sp = 0;
+        s_ref[0] = rc.x; s_cnt[0] = 0; s_d[0] = ds; sp = 1;
+        while (sp > 0) {
+            --sp;
+            int ref = s_ref[sp];
+            const int cnt = s_cnt[sp];
+            if (s_d[sp] > L.kth()) continue;
+            if (cnt > 0) {
+                scan_leaf<DC, KC>(T.bucket, ref, cnt, q, L);
+                continue;
+            }
+            for (;;) {
+                float r[4 * NW];
+                const float4 *np = T.nodes + (size_t)ref * NW;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    float4 f = __ldg(np + w);
+                    r[4 * w] = f.x; r[4 * w + 1] = f.y; r[4 * w + 2] = f.z; r[4 * w + 3] = f.w;
+                }
+                const int *ri = reinterpret_cast<const int *>(r + 4 * DC);
+                const int r0 = ri[0], c0 = ri[1], r1 = ri[2], c1 = ri[3];
+                const float d0 = boxdist<DC>(q, r, r + DC);
+                const float d1 = boxdist<DC>(q, r + 2 * DC, r + 3 * DC);
+                const bool sw = d1 < d0;
+                const float dn = sw ? d1 : d0, df = sw ? d0 : d1;
+                const int rn = sw ? r1 : r0, cn = sw ? c1 : c0;
+                const int rf = sw ? r0 : r1, cf = sw ? c0 : c1;
+                const float kth = L.kth();
+                if (cf >= 0 && df <= kth && sp < KNN_STACK) {
+                    s_ref[sp] = rf; s_cnt[sp] = cf; s_d[sp] = df; ++sp;
+                }
+                if (cn >= 0 && dn <= kth) {
+                    if (cn > 0) {
+                        scan_leaf<DC, KC>(T.bucket, rn, cn, q, L);
+                        break;
+                    }
+                    ref = rn;
+                    continue;
+                }
+                break;
+            }
+        }
+    }
+}
+
 // queries: row-major m*dim (NULL when self_bucket is given).
 // self_bucket: the tree's own bucket entries as queries (all-kNN); the
 // output row is then the entry's id.
@@ -550,7 +637,11 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
     }
     KList<KC> L;
     L.init(k);
-    for (int t = 0; t < ntrees; ++t) search_tree<DC, KC>(trees[t], q, L);
+    if (self_bucket && trees[0].leaf_parent && trees[0].parent) {
+        search_self_up<DC, KC>(trees[0], qi, q, L);
+    } else {
+        for (int t = 0; t < ntrees; ++t) search_tree<DC, KC>(trees[t], q, L);
+    }
     int32_t *oi = out_idx + row * k;
     float *od = out_dist + row * k;
 #pragma unroll
