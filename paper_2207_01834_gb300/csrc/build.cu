@@ -86,16 +86,154 @@ __global__ void __launch_bounds__(BT) k_pack(const float *__restrict__ src, cons
     }
 }
 
+// Device-side control block of the level loop: the host enqueues levels with
+// launch sizes from upper bounds and never waits on a count; kernels read the
+// live values here and do nothing once the loop is done.
+enum { CTL_S = 0, CTL_NB, CTL_FIN, CTL_DONE, CTL_SCATTERS, CTL_LEVELS, CTL_ROOT_SPLIT, CTL_WORDS };
+
+constexpr int FT_THREADS = 256, FT_ITEMS = 16, FT_TILE = FT_THREADS * FT_ITEMS;
+
+template <int DC>
+__device__ __forceinline__ int point_flag(const float *pf, int64_t i, const int *seg_of, const int *split_flag,
+                                          const int *sdim, const float *sval) {
+    constexpr int W = bucket_w(DC);
+    const int s = seg_of[i];
+    if (s < 0 || !split_flag[s]) return 0;
+    return pf[i * 4 * W + sdim[s]] < sval[s];
+}
+
+__device__ __forceinline__ int ft_block_excl(int v, int *wsum, int *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) wsum[lane] = w;
+    }
+    __syncthreads();
+    const int off = warp ? wsum[warp - 1] : 0;
+    *total = wsum[nw - 1];
+    __syncthreads();
+    return off + x - v;
+}
+
+// Exclusive scan of the "goes left" flags of all points, flags computed on
+// the fly (reduce / top / down).  Skipped when this level splits nothing.
+template <int DC>
+__global__ void __launch_bounds__(FT_THREADS) k_fscan_reduce(int64_t n, const float4 *__restrict__ P,
+                                                             const int *__restrict__ seg_of,
+                                                             const int *__restrict__ split_flag,
+                                                             const int *__restrict__ sdim,
+                                                             const float *__restrict__ sval,
+                                                             const int *__restrict__ T, int *__restrict__ bsum) {
+    if (*T == 0) return;
+    __shared__ int wsum[32];
+    const float *pf = reinterpret_cast<const float *>(P);
+    const int64_t base = (int64_t)blockIdx.x * FT_TILE;
+    int sum = 0;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < FT_TILE; j += FT_THREADS) {
+        const int64_t i = base + j;
+        if (i < n) sum += point_flag<DC>(pf, i, seg_of, split_flag, sdim, sval);
+    }
+    int tot;
+    ft_block_excl(sum, wsum, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_fscan_top(int *__restrict__ bsum, int nb, const int *__restrict__ T) {
+    if (*T == 0) return;
+    __shared__ int wsum[32];
+    int carry = 0;
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? bsum[i] : 0;
+        int tot;
+        const int ex = ft_block_excl(v, wsum, &tot);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+template <int DC>
+__global__ void __launch_bounds__(FT_THREADS) k_fscan_down(int64_t n, const float4 *__restrict__ P,
+                                                           const int *__restrict__ seg_of,
+                                                           const int *__restrict__ split_flag,
+                                                           const int *__restrict__ sdim,
+                                                           const float *__restrict__ sval,
+                                                           const int *__restrict__ T, const int *__restrict__ bsum,
+                                                           int nb, int *__restrict__ pre) {
+    if (*T == 0) return;
+    __shared__ int tile[FT_TILE];
+    __shared__ int wsum[32];
+    const float *pf = reinterpret_cast<const float *>(P);
+    const int64_t base = (int64_t)blockIdx.x * FT_TILE;
+    for (int j = threadIdx.x; j < FT_TILE; j += FT_THREADS) {
+        const int64_t i = base + j;
+        tile[j] = i < n ? point_flag<DC>(pf, i, seg_of, split_flag, sdim, sval) : 0;
+    }
+    __syncthreads();
+    int loc[FT_ITEMS];
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < FT_ITEMS; ++j) {
+        loc[j] = sum;
+        sum += tile[threadIdx.x * FT_ITEMS + j];
+    }
+    int tot;
+    const int ex = ft_block_excl(sum, wsum, &tot);
+    const int off = bsum[blockIdx.x] + ex;
+#pragma unroll
+    for (int j = 0; j < FT_ITEMS; ++j) tile[threadIdx.x * FT_ITEMS + j] = off + loc[j];
+    __syncthreads();
+    for (int j = threadIdx.x; j < FT_TILE; j += FT_THREADS) {
+        const int64_t i = base + j;
+        if (i < n) pre[i] = tile[j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) pre[n] = bsum[nb];
+}
+
+// End of a level: advance the control block (one thread).
+__global__ void k_level_end(int *ctl, const int *__restrict__ split_total, const int *__restrict__ fin_total,
+                            int level) {
+    if (ctl[CTL_DONE]) return;
+    const int T = *split_total;
+    ctl[CTL_NB] += T;
+    ctl[CTL_FIN] += *fin_total;
+    ctl[CTL_S] = 2 * T;
+    if (level == 0) ctl[CTL_ROOT_SPLIT] = T > 0;
+    if (T > 0) ctl[CTL_SCATTERS] += 1;
+    else { ctl[CTL_DONE] = 1; ctl[CTL_LEVELS] = level; }
+}
+
 // Decide, per segment, leaf or split; for a split pick the widest dimension
 // of the tight box (lowest index on ties) and its midpoint.
 template <int DC>
-__global__ void k_classify(int S, const int *__restrict__ start, const int *__restrict__ end,
+__global__ void k_classify(int S_max, const int *__restrict__ ctl, const int *__restrict__ start, const int *__restrict__ end,
                            const int *__restrict__ depth, const int *__restrict__ lo,
                            const int *__restrict__ hi, int leaf, int depth_cap, int fin_threshold,
                            int *__restrict__ split_flag, int *__restrict__ fin_flag, int *__restrict__ sdim,
                            float *__restrict__ sval) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+    if (s >= S_max) return;
+    if (ctl[CTL_DONE] || s >= ctl[CTL_S]) {   // padding up to the launch bound (or loop over)
+        split_flag[s] = 0;
+        fin_flag[s] = 0;
+        return;
+    }
     const int size = end[s] - start[s];
     int flag = 0, bd = 0;
     float bv = 0.f;
@@ -126,18 +264,19 @@ __global__ void k_classify(int S, const int *__restrict__ start, const int *__re
 // Write each segment into its parent's child slot (tight box + reference),
 // record split nodes and prepare the next level's child segments.
 template <int DC>
-__global__ void k_link(int S, const int *__restrict__ start, const int *__restrict__ end,
+__global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__restrict__ start, const int *__restrict__ end,
                        const int *__restrict__ parent, const int *__restrict__ side,
                        const int *__restrict__ depth, const int *__restrict__ lo, const int *__restrict__ hi,
                        const int *__restrict__ split_flag, const int *__restrict__ split_rank,
-                       const int *__restrict__ sdim, const float *__restrict__ sval, int node_base,
+                       const int *__restrict__ sdim, const float *__restrict__ sval,
                        float4 *__restrict__ nodes, int *__restrict__ n_sdim, float *__restrict__ n_sval,
                        int2 *__restrict__ n_range, int *__restrict__ nx_parent, int *__restrict__ nx_side,
                        int *__restrict__ nx_depth, int *__restrict__ nx_lo, int *__restrict__ nx_hi,
-                       const int *__restrict__ fin_flag, const int *__restrict__ fin_rank, int fin_base, Segs fin,
-                       int *__restrict__ n_parent, int *__restrict__ leaf_parent) {
+                       const int *__restrict__ fin_flag, const int *__restrict__ fin_rank, Segs fin,
+                       int *__restrict__ n_parent) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+    if (s >= S_max || ctl[CTL_DONE] || s >= ctl[CTL_S]) return;
+    const int node_base = ctl[CTL_NB], fin_base = ctl[CTL_FIN];
     const int st = start[s], size = end[s] - st;
     const int p = parent[s];
     const bool split = split_flag[s] != 0;
@@ -224,9 +363,12 @@ __global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restr
                                                 const int *__restrict__ split_flag,
                                                 const int *__restrict__ split_rank, const int *__restrict__ pre,
                                                 int *__restrict__ nx_start, int *__restrict__ nx_end,
-                                                int *__restrict__ nx_lo, int *__restrict__ nx_hi, int nchild) {
+                                                int *__restrict__ nx_lo, int *__restrict__ nx_hi,
+                                                const int *__restrict__ split_total) {
     constexpr int W = bucket_w(DC);
     const int lane = threadIdx.x & 31;
+    const int nchild = 2 * *split_total;
+    if (nchild == 0) return;
     // With few children (top levels) every block first reduces the boxes in
     // shared memory and then adds one global atomic per child and dimension;
     // otherwise warps go straight to global memory.
@@ -322,11 +464,12 @@ __global__ void k_fin_words(Segs fin, int count, int leaf, int *units) {
 
 template <int DC>
 __global__ void __launch_bounds__(FIN_NT, 1024 / FIN_NT) k_finish(Segs fin, float4 *P, float4 *Q, int *scratch,
-                                                   const int *__restrict__ unit_off, int leaf, int nb, float4 *nodes,
+                                                   const int *__restrict__ unit_off, int leaf, const int *ctl, float4 *nodes,
                                                    int *n_sdim, float *n_sval, int2 *n_range, int *root_rec,
                                                    int *depth_max, int *n_parent, int *leaf_parent) {
     __shared__ int s_w[33];
     const int f = blockIdx.x;
+    const int nb = ctl[CTL_NB];
     const int st = fin.start[f], en = fin.end[f];
     const CtaTree r = cta_build_tree<DC, FIN_NT>(P, Q, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC,
                                                  scratch + (long long)unit_off[f] * 32, leaf, nb + st,
@@ -414,11 +557,10 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     // has at most 2*floor(n/(leaf+1)) segments.
     const int seg_cap = (int)std::max<int64_t>(2, 2 * (n / (leaf + 1)) + 2);
 
-    Scratch sP1, sSeg0, sSeg1, sFlag, sPre, sSegA, sSegB, sLvl, sHost;
+    Scratch sP1, sSeg0, sSeg1, sPre, sSegA, sSegB, sLvl, sBsum, sCtl;
     PG_TRY(sP1.alloc(sizeof(float4) * W * (size_t)n, s));
     PG_TRY(sSeg0.alloc(sizeof(int) * (size_t)n, s));
     PG_TRY(sSeg1.alloc(sizeof(int) * (size_t)n, s));
-    PG_TRY(sFlag.alloc(sizeof(int) * (size_t)n, s));
     PG_TRY(sPre.alloc(sizeof(int) * (size_t)(n + 1), s));
     const size_t seg_words = (size_t)seg_cap * (5 + 2 * DC);
     PG_TRY(sSegA.alloc(sizeof(int) * seg_words, s));
@@ -431,6 +573,10 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     float *sval = reinterpret_cast<float *>(sdim + seg_cap);
     int *fin_flag = sdim + 2 * seg_cap;
     int *fin_rank = fin_flag + seg_cap;
+    const int ft_tiles = std::max(1, ceil_div_i(n, FT_TILE));
+    PG_TRY(sBsum.alloc(sizeof(int) * (size_t)(ft_tiles + 1), s));
+    PG_TRY(sCtl.alloc(sizeof(int) * CTL_WORDS, s));
+    int *ctl = sCtl.as<int>();
     // segments handed to the block-scope finisher (disjoint, > leaf points each)
     const int fin_cap = (int)(n / (leaf + 1) + 1);
     Scratch sFin;
@@ -441,8 +587,6 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         fin.start = b; fin.end = b + fin_cap; fin.parent = b + 2 * fin_cap; fin.side = b + 3 * fin_cap;
         fin.depth = b + 4 * fin_cap; fin.lo = b + 5 * fin_cap; fin.hi = b + (5 + DC) * fin_cap;
     }
-    int fin_total = 0;
-
     auto carve = [&](Scratch &sc) {
         int *b = sc.as<int>();
         Segs g;
@@ -456,7 +600,14 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     int *seg_of = sSeg0.as<int>(), *seg_of_nx = sSeg1.as<int>();
     PG_CUDA(cudaMemsetAsync(seg_of, 0, sizeof(int) * (size_t)n, s));   // all in segment 0
     if (!t->leaf_parent) PG_TRY(dalloc_n(&t->leaf_parent, (size_t)n, s));
-    PG_TRY(grow_nodes(t, 16, s));   // the parent array must exist for the first link
+    // Node slots: every global split holds more than kFinThreshold points (at
+    // most n/(threshold+1) per level), and finisher segment [st, en) reserves
+    // slots [nb + st, nb + en) after the nb global nodes.  Unused slots stay
+    // all-ones (cnt = -1).
+    const int64_t slots = (int64_t)(PG_DEPTH_CAP + 1) * (n / (kFinThreshold + 1)) + 64 + n;
+    if (slots >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "tree build: too many node slots");
+    PG_TRY(grow_nodes(t, (int)slots, s));
+    PG_CUDA(cudaMemsetAsync(t->nodes, 0xff, sizeof(float4) * node_w(DC) * (size_t)slots, s));
 
     // level 0: one segment covering everything, box reduced by k_pack
     {
@@ -468,64 +619,65 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         PG_CUDA(cudaMemcpyAsync(cur.depth, &h[4], sizeof(int), cudaMemcpyHostToDevice, s));
         PG_CUDA(cudaMemcpyAsync(cur.lo, box, sizeof(int) * DC, cudaMemcpyDeviceToDevice, s));
         PG_CUDA(cudaMemcpyAsync(cur.hi, box + DC, sizeof(int) * DC, cudaMemcpyDeviceToDevice, s));
+        int c[CTL_WORDS] = {1, 0, 0, 0, 0, 0, 0};
+        PG_CUDA(cudaMemcpyAsync(ctl, c, sizeof(c), cudaMemcpyHostToDevice, s));
     }
-    int hT[2] = {0, 0};
-
-    int S = 1;
+    // The host enqueues levels without waiting; it starts checking for the
+    // end around the level where uniform data would stop.
+    int est = 1;
+    while (((int64_t)kFinThreshold << (est - 1)) < n && est < PG_DEPTH_CAP) ++est;
+    int hctl[CTL_WORDS] = {0};
     int level = 0;
-    int node_base = 0;
-    bool root_split = false;
-    t->num_nodes = 0;
-    for (;;) {
-        if (level > PG_DEPTH_CAP + 1) return fail(PG_ECUDA, "tree build: level count exceeded the depth cap");
-        const int gs = ceil_div_i(S, BT);
-        k_classify<DC><<<gs, BT, 0, s>>>(S, cur.start, cur.end, cur.depth, cur.lo, cur.hi, leaf, PG_DEPTH_CAP,
-                                         kFinThreshold, split_flag, fin_flag, sdim, sval);
+    for (; level <= PG_DEPTH_CAP + 1; ++level) {
+        const int S_max = (int)std::min<int64_t>((int64_t)1 << std::min(level, 30), seg_cap);
+        const int gs = ceil_div_i(S_max, BT);
+        k_classify<DC><<<gs, BT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.depth, cur.lo, cur.hi, leaf,
+                                         PG_DEPTH_CAP, kFinThreshold, split_flag, fin_flag, sdim, sval);
         count_launch();
-        PG_TRY(exclusive_scan(split_flag, split_rank, S, s));
-        PG_TRY(exclusive_scan(fin_flag, fin_rank, S, s));
-        PG_CUDA(cudaMemcpyAsync(hT, split_rank + S, sizeof(int), cudaMemcpyDeviceToHost, s));
-        PG_CUDA(cudaMemcpyAsync(hT + 1, fin_rank + S, sizeof(int), cudaMemcpyDeviceToHost, s));
-        PG_CUDA(cudaStreamSynchronize(s));
-        const int T = hT[0];
-        if (level == 0) root_split = T > 0;
-        PG_TRY(grow_nodes(t, node_base + T, s));
-        k_link<DC><<<gs, BT, 0, s>>>(S, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo, cur.hi,
-                                     split_flag, split_rank, sdim, sval, node_base, t->nodes, t->split_dim,
-                                     t->split_val, t->node_range, nxt.parent, nxt.side, nxt.depth, nxt.lo,
-                                     nxt.hi, fin_flag, fin_rank, fin_total, fin, t->parent, t->leaf_parent);
+        PG_TRY(exclusive_scan(split_flag, split_rank, S_max, s));
+        PG_TRY(exclusive_scan(fin_flag, fin_rank, S_max, s));
+        k_link<DC><<<gs, BT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo,
+                                     cur.hi, split_flag, split_rank, sdim, sval, t->nodes, t->split_dim,
+                                     t->split_val, t->node_range, nxt.parent, nxt.side, nxt.depth, nxt.lo, nxt.hi,
+                                     fin_flag, fin_rank, fin, t->parent);
         count_launch();
-        PG_TRY(check_launch("build level"));
-        fin_total += hT[1];
-        if (T == 0) break;
-        k_flag<DC><<<grid_pts, BT, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, sFlag.as<int>());
+        const int *T = split_rank + S_max;
+        k_fscan_reduce<DC><<<ft_tiles, FT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<int>());
+        k_fscan_top<<<1, 1024, 0, s>>>(sBsum.as<int>(), ft_tiles, T);
+        k_fscan_down<DC><<<ft_tiles, FT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<int>(),
+                                                          ft_tiles, sPre.as<int>());
         count_launch();
-        PG_TRY(exclusive_scan(sFlag.as<int>(), sPre.as<int>(), n, s));
+        count_launch();
+        count_launch();
         {
             KTimer kt("build_scatter", s);
             k_scatter<DC><<<grid_pts, BT, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
-                                                  split_rank, sPre.as<int>(), nxt.start, nxt.end, nxt.lo, nxt.hi,
-                                                  2 * T);
+                                                  split_rank, sPre.as<int>(), nxt.start, nxt.end, nxt.lo, nxt.hi, T);
             count_launch();
         }
-        PG_TRY(check_launch("build scatter"));
-        node_base += T;
-        t->num_nodes = node_base;
+        k_level_end<<<1, 1, 0, s>>>(ctl, T, fin_rank + S_max, level);
+        count_launch();
+        PG_TRY(check_launch("build level"));
         std::swap(P, Q);
         std::swap(seg_of, seg_of_nx);
         std::swap(cur, nxt);
-        S = 2 * T;
-        ++level;
+        if (level + 1 >= est) {
+            PG_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(hctl), cudaMemcpyDeviceToHost, s));
+            PG_CUDA(cudaStreamSynchronize(s));
+            if (hctl[CTL_DONE]) break;
+        }
     }
-    t->depth = level;
+    if (!hctl[CTL_DONE]) return fail(PG_ECUDA, "tree build: level count exceeded the depth cap");
+    const int nb = hctl[CTL_NB], fin_total = hctl[CTL_FIN];
+    const bool root_split = hctl[CTL_ROOT_SPLIT] != 0;
+    // the buffers alternate once per level that split something
+    P = (hctl[CTL_SCATTERS] % 2 == 0) ? P0 : sP1.as<float4>();
+    Q = (P == P0) ? sP1.as<float4>() : P0;
+    t->num_nodes = fin_total > 0 ? nb + (int)n : nb;
+    t->depth = hctl[CTL_LEVELS];
     t->root_ref = 0;
     t->root_cnt = root_split ? 0 : (int)n;
     if (fin_total > 0) {
-        // every finisher segment reserves node slots [node_base + st, node_base + en)
-        const int nb = node_base;
-        PG_TRY(grow_nodes(t, nb + (int)n, s));
-        PG_CUDA(cudaMemsetAsync(t->nodes + (size_t)nb * node_w(DC), 0xff, sizeof(float4) * node_w(DC) * (size_t)n, s));
-        t->num_nodes = nb + (int)n;
         Scratch sUnits, sOff, sScr, sRec;
         PG_TRY(sUnits.alloc(sizeof(int) * (size_t)fin_total, s));
         PG_TRY(sOff.alloc(sizeof(int) * (size_t)(fin_total + 1), s));
@@ -541,7 +693,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         PG_CUDA(cudaMemsetAsync(rec, 0, sizeof(int) * 3, s));
         {
             KTimer kt("build_finish", s);
-            k_finish<DC><<<fin_total, FIN_NT, 0, s>>>(fin, P, Q, sScr.as<int>(), sOff.as<int>(), leaf, nb, t->nodes,
+            k_finish<DC><<<fin_total, FIN_NT, 0, s>>>(fin, P, Q, sScr.as<int>(), sOff.as<int>(), leaf, ctl, t->nodes,
                                                        t->split_dim, t->split_val, t->node_range, rec, rec + 2,
                                                        t->parent, t->leaf_parent);
             count_launch();
