@@ -20,14 +20,17 @@ namespace {
 
 constexpr int BT = 256;
 
+// Coordinate loops run to the dimension class DC (compile time) and skip
+// c >= dim, so registers and instructions follow the real dimension.
+template <int DC>
 __global__ void k_bwd_queries(const float *__restrict__ data, int64_t n, const float *__restrict__ queries, int64_t m,
                               int dim, int k, const int32_t *__restrict__ idx, const float *__restrict__ g,
                               float *__restrict__ gq) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    float q[PG_MAX_DIM], acc[PG_MAX_DIM];
+    float q[DC], acc[DC];
 #pragma unroll
-    for (int c = 0; c < PG_MAX_DIM; ++c) {
+    for (int c = 0; c < DC; ++c) {
         q[c] = c < dim ? queries[i * dim + c] : 0.f;
         acc[c] = 0.f;
     }
@@ -36,11 +39,11 @@ __global__ void k_bwd_queries(const float *__restrict__ data, int64_t n, const f
         if (t < 0 || t >= n) continue;   // padding (or out of range): no contribution
         const float w = 2.f * g[i * k + j];
 #pragma unroll
-        for (int c = 0; c < PG_MAX_DIM; ++c)
+        for (int c = 0; c < DC; ++c)
             if (c < dim) acc[c] = __fmaf_rn(w, __fsub_rn(q[c], data[(int64_t)t * dim + c]), acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < PG_MAX_DIM; ++c)
+    for (int c = 0; c < DC; ++c)
         if (c < dim) gq[i * dim + c] = acc[c];
 }
 
@@ -62,14 +65,15 @@ __global__ void k_bwd_bounds(const uint32_t *__restrict__ skeys, int64_t P, uint
     if (x == P - 1 || skeys[x + 1] != key) hi[key] = (int)(x + 1);
 }
 
+template <int DC>
 __global__ void k_bwd_data(const float *__restrict__ data, const float *__restrict__ queries, int64_t n, int dim,
                            int k, const uint32_t *__restrict__ svals, const float *__restrict__ g,
                            const int *__restrict__ lo, const int *__restrict__ hi, float *__restrict__ gp) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    float p[PG_MAX_DIM], acc[PG_MAX_DIM];
+    float p[DC], acc[DC];
 #pragma unroll
-    for (int c = 0; c < PG_MAX_DIM; ++c) {
+    for (int c = 0; c < DC; ++c) {
         p[c] = c < dim ? data[t * dim + c] : 0.f;
         acc[c] = 0.f;
     }
@@ -79,15 +83,41 @@ __global__ void k_bwd_data(const float *__restrict__ data, const float *__restri
         const int64_t i = pr / (uint32_t)k;
         const float w = -2.f * g[pr];
 #pragma unroll
-        for (int c = 0; c < PG_MAX_DIM; ++c)
+        for (int c = 0; c < DC; ++c)
             if (c < dim) acc[c] = __fmaf_rn(w, __fsub_rn(queries[i * dim + c], p[c]), acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < PG_MAX_DIM; ++c)
+    for (int c = 0; c < DC; ++c)
         if (c < dim) gp[t * dim + c] = acc[c];
 }
 
 inline int grid_of(int64_t n) { return std::max(1, ceil_div_i(n, BT)); }
+
+#define PG_DC_SWITCH(dim, CASE)                                                             \
+    switch (dim_class(dim)) {                                                               \
+        CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(12) CASE(16)           \
+        default: return fail(PG_EUNSUPPORTED, "dimension class");                          \
+    }
+
+pg_status launch_bwd_queries(const float *data, int64_t n, const float *queries, int64_t m, int dim, int k,
+                             const int32_t *idx, const float *g, float *gq, cudaStream_t s) {
+#define PG_CASE(D)                                                                                  \
+    case D: k_bwd_queries<D><<<grid_of(m), BT, 0, s>>>(data, n, queries, m, dim, k, idx, g, gq); break;
+    PG_DC_SWITCH(dim, PG_CASE)
+#undef PG_CASE
+    count_launch();
+    return PG_OK;
+}
+
+pg_status launch_bwd_data(const float *data, const float *queries, int64_t n, int dim, int k, const uint32_t *sv,
+                          const float *g, const int *lo, const int *hi, float *gp, cudaStream_t s) {
+#define PG_CASE(D)                                                                                  \
+    case D: k_bwd_data<D><<<grid_of(n), BT, 0, s>>>(data, queries, n, dim, k, sv, g, lo, hi, gp); break;
+    PG_DC_SWITCH(dim, PG_CASE)
+#undef PG_CASE
+    count_launch();
+    return PG_OK;
+}
 
 }  // namespace
 
@@ -101,8 +131,7 @@ pg_status knn_backward_run(const float *data, int64_t n, const float *queries, i
                            const int32_t *idx, const float *g, float *gq, float *gp, void *scratch,
                            cudaStream_t s) {
     if (gq && m > 0) {
-        k_bwd_queries<<<grid_of(m), BT, 0, s>>>(data, n, queries, m, dim, k, idx, g, gq);
-        count_launch();
+        PG_TRY(launch_bwd_queries(data, n, queries, m, dim, k, idx, g, gq, s));
     }
     if (gp && n > 0) {
         const int64_t P = m * k;
@@ -121,8 +150,7 @@ pg_status knn_backward_run(const float *data, int64_t n, const float *queries, i
             count_launch();
         }
         KTimer kt("knn_backward_data", s);
-        k_bwd_data<<<grid_of(n), BT, 0, s>>>(data, queries, n, dim, k, sv, g, lo, hi, gp);
-        count_launch();
+        PG_TRY(launch_bwd_data(data, queries, n, dim, k, sv, g, lo, hi, gp, s));
     }
     return check_launch("knn backward");
 }
@@ -133,8 +161,7 @@ pg_status knn_backward_run_ws(const float *data, int64_t n, const float *queries
                               const int32_t *idx, const float *g, float *gq, float *gp, void *scratch,
                               int *radix_ws, cudaStream_t s) {
     if (gq && m > 0) {
-        k_bwd_queries<<<grid_of(m), BT, 0, s>>>(data, n, queries, m, dim, k, idx, g, gq);
-        count_launch();
+        PG_TRY(launch_bwd_queries(data, n, queries, m, dim, k, idx, g, gq, s));
     }
     if (gp && n > 0) {
         const int64_t P = m * k;
@@ -152,8 +179,7 @@ pg_status knn_backward_run_ws(const float *data, int64_t n, const float *queries
             k_bwd_bounds<<<grid_of(P), BT, 0, s>>>(sk, P, (uint32_t)n, lo, hi);
             count_launch();
         }
-        k_bwd_data<<<grid_of(n), BT, 0, s>>>(data, queries, n, dim, k, sv, g, lo, hi, gp);
-        count_launch();
+        PG_TRY(launch_bwd_data(data, queries, n, dim, k, sv, g, lo, hi, gp, s));
     }
     return check_launch("knn backward");
 }

@@ -72,16 +72,22 @@ __global__ void k_bbounds(const uint32_t *__restrict__ sk, int64_t P, uint32_t n
 // Gradient of sum_i g_i loss_i for the rows of one array X (the other array
 // is Y):  direct part from X's own k neighbours in Y, then the contributions
 // of every Y row that selected this X row, in ascending (row, slot) order.
+// Rows selected more than kHeavy times are finished by k_bgrad_heavy (one
+// warp per row) so that a few hub points do not hold whole warps back.
+constexpr int kHeavy = 64;
+
+template <int DC>
 __global__ void k_bgrad(const float *__restrict__ X, int64_t nx, const float *__restrict__ Y, int dim, int k,
                         const int32_t *__restrict__ idx_xy, const int *__restrict__ row_pair_x,
                         const int *__restrict__ row_pair_y, const long long *__restrict__ off_y,
                         const float *__restrict__ g, const uint32_t *__restrict__ sv_yx, const int *__restrict__ lo,
-                        const int *__restrict__ hi, float *__restrict__ gx) {
+                        const int *__restrict__ hi, float *__restrict__ gx, int *__restrict__ heavy,
+                        int *__restrict__ nheavy) {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nx) return;
-    float p[PG_MAX_DIM], acc[PG_MAX_DIM];
+    float p[DC], acc[DC];
 #pragma unroll
-    for (int c = 0; c < PG_MAX_DIM; ++c) {
+    for (int c = 0; c < DC; ++c) {
         p[c] = c < dim ? X[x * dim + c] : 0.f;
         acc[c] = 0.f;
     }
@@ -93,20 +99,67 @@ __global__ void k_bgrad(const float *__restrict__ X, int64_t nx, const float *__
         if (t < 0 || t >= lim) continue;
         const int64_t yr = base + t;
 #pragma unroll
-        for (int c = 0; c < PG_MAX_DIM; ++c)
+        for (int c = 0; c < DC; ++c)
             if (c < dim) acc[c] = __fmaf_rn(w, __fsub_rn(p[c], Y[yr * dim + c]), acc[c]);
     }
-    for (int e = lo[x]; e < hi[x]; ++e) {
-        const uint32_t v = sv_yx[e];
-        const int64_t yr = v / (uint32_t)k;
-        const float wy = -2.f * g[row_pair_y[yr]];
+    const int e0 = lo[x], e1 = hi[x];
+    if (e1 - e0 > kHeavy) {
+        heavy[atomicAdd(nheavy, 1)] = (int)x;     // list order does not affect any sum
+    } else {
+        for (int e = e0; e < e1; ++e) {
+            const uint32_t v = sv_yx[e];
+            const int64_t yr = v / (uint32_t)k;
+            const float wy = -2.f * g[row_pair_y[yr]];
 #pragma unroll
-        for (int c = 0; c < PG_MAX_DIM; ++c)
-            if (c < dim) acc[c] = __fmaf_rn(wy, __fsub_rn(Y[yr * dim + c], p[c]), acc[c]);
+            for (int c = 0; c < DC; ++c)
+                if (c < dim) acc[c] = __fmaf_rn(wy, __fsub_rn(Y[yr * dim + c], p[c]), acc[c]);
+        }
     }
 #pragma unroll
-    for (int c = 0; c < PG_MAX_DIM; ++c)
+    for (int c = 0; c < DC; ++c)
         if (c < dim) gx[x * dim + c] = acc[c];
+}
+
+// One warp per heavy row: lane l sums entries l, l+32, ... in order, then a
+// fixed butterfly adds the lanes; the row's direct part (already in gx) is
+// added last.  The order is the same on every run.
+template <int DC>
+__global__ void k_bgrad_heavy(const float *__restrict__ X, const float *__restrict__ Y, int dim, int k,
+                              const int *__restrict__ row_pair_y, const float *__restrict__ g,
+                              const uint32_t *__restrict__ sv_yx, const int *__restrict__ lo,
+                              const int *__restrict__ hi, float *__restrict__ gx, const int *__restrict__ heavy,
+                              const int *__restrict__ nheavy) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int cnt = *nheavy;
+    for (int64_t h = wid; h < cnt; h += nw) {
+        const int64_t x = heavy[h];
+        float p[DC], acc[DC];
+#pragma unroll
+        for (int c = 0; c < DC; ++c) {
+            p[c] = c < dim ? X[x * dim + c] : 0.f;
+            acc[c] = 0.f;
+        }
+        for (int e = lo[x] + lane; e < hi[x]; e += 32) {
+            const uint32_t v = sv_yx[e];
+            const int64_t yr = v / (uint32_t)k;
+            const float wy = -2.f * g[row_pair_y[yr]];
+#pragma unroll
+            for (int c = 0; c < DC; ++c)
+                if (c < dim) acc[c] = __fmaf_rn(wy, __fsub_rn(Y[yr * dim + c], p[c]), acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < DC; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[c] = __fadd_rn(acc[c], __shfl_xor_sync(0xffffffffu, acc[c], o));
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < DC; ++c)
+                if (c < dim) gx[x * dim + c] = __fadd_rn(gx[x * dim + c], acc[c]);
+        }
+    }
 }
 
 inline int grid_of(int64_t n) { return std::max(1, ceil_div_i(n, BT)); }
@@ -379,9 +432,10 @@ extern "C" pg_status pg_batched_chamfer_backward(const float *a, const int64_t *
     count_launch();
     const int64_t Pab = Na * k, Pba = Nb * k, Pm = std::max(Pab, Pba);
     // keys, vals, two temporaries (for the larger direction) + bounds for a and b
-    PG_TRY(sc.alloc(sizeof(uint32_t) * (size_t)(4 * Pm) + sizeof(int) * (size_t)(2 * std::max(Na, Nb)) + 256, s));
+    PG_TRY(sc.alloc(sizeof(uint32_t) * (size_t)(4 * Pm) + sizeof(int) * (size_t)(3 * std::max(Na, Nb) + 1) + 256, s));
     uint32_t *keys = sc.as<uint32_t>(), *vals = keys + Pm, *tk = vals + Pm, *tv = tk + Pm;
     int *lo = reinterpret_cast<int *>(tv + Pm), *hi = lo + std::max(Na, Nb);
+    int *heavy = hi + std::max(Na, Nb), *nheavy = heavy + std::max(Na, Nb);
     auto bits_for = [](int64_t n) { int b = 1; while (b < 32 && ((int64_t)1 << b) <= n) ++b; return b; };
     // grad_b: b rows' own neighbours in a (idx_ba) + a rows that selected them (idx_ab)
     for (int side = 0; side < 2; ++side) {
@@ -399,9 +453,27 @@ extern "C" pg_status pg_batched_chamfer_backward(const float *a, const int64_t *
         k_bbounds<<<grid_of(P), BT, 0, s>>>(sk, P, (uint32_t)nx, lo, lo + std::max(Na, Nb));
         count_launch();
         KTimer kt("batched_backward_grad", s);
-        k_bgrad<<<grid_of(nx), BT, 0, s>>>(for_b ? b : a, nx, for_b ? a : b, dim, k, for_b ? idx_ba : idx_ab,
-                                            for_b ? rpb : rpa, rpy, for_b ? aoff : boff, grad_loss, sv, lo,
-                                            lo + std::max(Na, Nb), for_b ? grad_b : grad_a);
+        PG_CUDA(cudaMemsetAsync(nheavy, 0, sizeof(int), s));
+        const float *Xp = for_b ? b : a, *Yp = for_b ? a : b;
+        const int32_t *ixy = for_b ? idx_ba : idx_ab;
+        const int *rpx = for_b ? rpb : rpa;
+        const long long *offy = for_b ? aoff : boff;
+        float *gxp = for_b ? grad_b : grad_a;
+        int *hi_arr = lo + std::max(Na, Nb);
+        const int hgrid = num_sms() * 8;
+        switch (dim_class(dim)) {
+#define PG_BG(D)                                                                                            \
+            case D:                                                                                         \
+                k_bgrad<D><<<grid_of(nx), BT, 0, s>>>(Xp, nx, Yp, dim, k, ixy, rpx, rpy, offy, grad_loss, sv, lo, \
+                                                      hi_arr, gxp, heavy, nheavy);                          \
+                k_bgrad_heavy<D><<<hgrid, BT, 0, s>>>(Xp, Yp, dim, k, rpy, grad_loss, sv, lo, hi_arr, gxp,  \
+                                                      heavy, nheavy);                                       \
+                break;
+            PG_BG(2) PG_BG(3) PG_BG(4) PG_BG(5) PG_BG(6) PG_BG(7) PG_BG(8) PG_BG(12) PG_BG(16)
+#undef PG_BG
+            default: return fail(PG_EUNSUPPORTED, "dimension class");
+        }
+        count_launch();
         count_launch();
         PG_TRY(check_launch("batched backward"));
     }
