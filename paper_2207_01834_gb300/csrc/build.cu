@@ -17,7 +17,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "cta_build.cuh"
+#include "cta_build_smem.cuh"
 #include "internal.h"
 
 namespace pg {
@@ -446,35 +446,23 @@ __global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restr
     }
 }
 
-#ifndef PG_FIN_NT
-#define PG_FIN_NT 256
-#endif
-constexpr int FIN_NT = PG_FIN_NT;   // threads of a finisher block
-constexpr int kFinThreshold = 16384;   // segments up to this size finish inside one block
+constexpr int FIN_NT = 256;                  // threads of a finisher block
+constexpr size_t kFinSmemBudget = 110 * 1024;   // shared memory of a finisher block (two blocks per SM)
 
-// Finisher scratch: segment f gets cta_scratch_words(n_f) ints at an offset
-// taken from an exclusive scan of the sizes in 32-int units (segments are
-// appended level by level, so their order is not bucket order).  Node slots
-// are reserved by bucket position: segment [st, en) may use [nb+st, nb+en).
+// Segments small enough for one block's shared memory are finished by the
+// in-block builder; node slots are reserved by bucket position: segment
+// [st, en) uses slots [nb + st, nb + en - 1).
 template <int DC>
-__global__ void k_fin_words(Segs fin, int count, int leaf, int *units) {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f < count) units[f] = (int)((cta_scratch_words(fin.end[f] - fin.start[f], leaf, DC) + 31) / 32);
-}
-
-template <int DC>
-__global__ void __launch_bounds__(FIN_NT, 1024 / FIN_NT) k_finish(Segs fin, float4 *P, float4 *Q, int *scratch,
-                                                   const int *__restrict__ unit_off, int leaf, const int *ctl, float4 *nodes,
-                                                   int *n_sdim, float *n_sval, int2 *n_range, int *root_rec,
-                                                   int *depth_max, int *n_parent, int *leaf_parent) {
-    __shared__ int s_w[33];
+__global__ void __launch_bounds__(FIN_NT, 2) k_finish(Segs fin, float4 *P, int leaf, int ns, int sc, const int *ctl,
+                                                      float4 *nodes, int *n_sdim, float *n_sval, int2 *n_range,
+                                                      int *root_rec, int *depth_max, int *n_parent) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int f = blockIdx.x;
     const int nb = ctl[CTL_NB];
     const int st = fin.start[f], en = fin.end[f];
-    const CtaTree r = cta_build_tree<DC, FIN_NT>(P, Q, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC,
-                                                 scratch + (long long)unit_off[f] * 32, leaf, nb + st,
-                                                 nodes, n_sdim, n_sval, n_range, s_w, fin.depth[f], n_parent,
-                                                 nullptr,
+    const CtaTree r = cta_build_smem<DC, FIN_NT>(P, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC, smem, ns,
+                                                 sc, leaf, nb + st, nodes, n_sdim, n_sval, n_range, fin.depth[f],
+                                                 n_parent, nullptr,
                                                  fin.parent[f] >= 0 ? 2 * fin.parent[f] + fin.side[f] : -1);
     if (threadIdx.x == 0) {
         const int p = fin.parent[f];
@@ -600,11 +588,15 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     int *seg_of = sSeg0.as<int>(), *seg_of_nx = sSeg1.as<int>();
     PG_CUDA(cudaMemsetAsync(seg_of, 0, sizeof(int) * (size_t)n, s));   // all in segment 0
     if (!t->leaf_parent) PG_TRY(dalloc_n(&t->leaf_parent, (size_t)n, s));
-    // Node slots: every global split holds more than kFinThreshold points (at
-    // most n/(threshold+1) per level), and finisher segment [st, en) reserves
-    // slots [nb + st, nb + en) after the nb global nodes.  Unused slots stay
+    // Segments of up to fin_max points are finished in one block's shared memory.
+    const int fin_max = smem_build_points(DC, leaf, kFinSmemBudget);
+    const int fin_sc = smem_seg_cap(fin_max, leaf);
+    const size_t fin_smem = smem_build_bytes(fin_max, fin_sc, DC);
+    // Node slots: every global split holds more than fin_max points (at most
+    // n/(fin_max+1) per level), and finisher segment [st, en) reserves slots
+    // [nb + st, nb + en) after the nb global nodes.  Unused slots stay
     // all-ones (cnt = -1).
-    const int64_t slots = (int64_t)(PG_DEPTH_CAP + 1) * (n / (kFinThreshold + 1)) + 64 + n;
+    const int64_t slots = (int64_t)(PG_DEPTH_CAP + 1) * (n / (fin_max + 1)) + 64 + n;
     if (slots >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "tree build: too many node slots");
     PG_TRY(grow_nodes(t, (int)slots, s));
     PG_CUDA(cudaMemsetAsync(t->nodes, 0xff, sizeof(float4) * node_w(DC) * (size_t)slots, s));
@@ -625,14 +617,14 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     // The host enqueues levels without waiting; it starts checking for the
     // end around the level where uniform data would stop.
     int est = 1;
-    while (((int64_t)kFinThreshold << (est - 1)) < n && est < PG_DEPTH_CAP) ++est;
+    while (((int64_t)fin_max << (est - 1)) < n && est < PG_DEPTH_CAP) ++est;
     int hctl[CTL_WORDS] = {0};
     int level = 0;
     for (; level <= PG_DEPTH_CAP + 1; ++level) {
         const int S_max = (int)std::min<int64_t>((int64_t)1 << std::min(level, 30), seg_cap);
         const int gs = ceil_div_i(S_max, BT);
         k_classify<DC><<<gs, BT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.depth, cur.lo, cur.hi, leaf,
-                                         PG_DEPTH_CAP, kFinThreshold, split_flag, fin_flag, sdim, sval);
+                                         PG_DEPTH_CAP, fin_max, split_flag, fin_flag, sdim, sval);
         count_launch();
         PG_TRY(exclusive_scan(split_flag, split_rank, S_max, s));
         PG_TRY(exclusive_scan(fin_flag, fin_rank, S_max, s));
@@ -672,30 +664,21 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     const bool root_split = hctl[CTL_ROOT_SPLIT] != 0;
     // the buffers alternate once per level that split something
     P = (hctl[CTL_SCATTERS] % 2 == 0) ? P0 : sP1.as<float4>();
-    Q = (P == P0) ? sP1.as<float4>() : P0;
     t->num_nodes = fin_total > 0 ? nb + (int)n : nb;
     t->depth = hctl[CTL_LEVELS];
     t->root_ref = 0;
     t->root_cnt = root_split ? 0 : (int)n;
     if (fin_total > 0) {
-        Scratch sUnits, sOff, sScr, sRec;
-        PG_TRY(sUnits.alloc(sizeof(int) * (size_t)fin_total, s));
-        PG_TRY(sOff.alloc(sizeof(int) * (size_t)(fin_total + 1), s));
-        k_fin_words<DC><<<ceil_div_i(fin_total, BT), BT, 0, s>>>(fin, fin_total, leaf, sUnits.as<int>());
-        count_launch();
-        PG_TRY(exclusive_scan(sUnits.as<int>(), sOff.as<int>(), fin_total, s));
-        int units = 0;
-        PG_CUDA(cudaMemcpyAsync(&units, sOff.as<int>() + fin_total, sizeof(int), cudaMemcpyDeviceToHost, s));
-        PG_CUDA(cudaStreamSynchronize(s));
-        PG_TRY(sScr.alloc(sizeof(int) * 32 * (size_t)units, s));
+        PG_CUDA(cudaFuncSetAttribute(k_finish<DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fin_smem));
+        Scratch sRec;
         PG_TRY(sRec.alloc(sizeof(int) * 3, s));
         int *rec = sRec.as<int>();
         PG_CUDA(cudaMemsetAsync(rec, 0, sizeof(int) * 3, s));
         {
             KTimer kt("build_finish", s);
-            k_finish<DC><<<fin_total, FIN_NT, 0, s>>>(fin, P, Q, sScr.as<int>(), sOff.as<int>(), leaf, ctl, t->nodes,
-                                                       t->split_dim, t->split_val, t->node_range, rec, rec + 2,
-                                                       t->parent, t->leaf_parent);
+            k_finish<DC><<<fin_total, FIN_NT, fin_smem, s>>>(fin, P, leaf, fin_max, fin_sc, ctl, t->nodes,
+                                                             t->split_dim, t->split_val, t->node_range, rec, rec + 2,
+                                                             t->parent);
             count_launch();
         }
         PG_TRY(check_launch("build finish"));

@@ -104,6 +104,11 @@ struct TreeDesc {
     float root_hi[PG_MAX_DIM];
 };
 
+// Result of building one tree inside one thread block.
+struct CtaTree {
+    int root_ref, root_cnt, nodes, depth;
+};
+
 // ---------------------------------------------------------------- float order
 // Monotone map float -> int so that integer min/max order equals float order.
 __device__ __forceinline__ int f2o(float f) {

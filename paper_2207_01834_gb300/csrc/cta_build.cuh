@@ -99,11 +99,6 @@ __device__ int cta_excl_scan(const int *in, int *out, int L, int *s_w) {
     return carry;
 }
 
-// Result of building one tree.
-struct CtaTree {
-    int root_ref, root_cnt, nodes, depth;
-};
-
 // Build a kd-tree over bucket entries P[s0, s1) (already packed, any order)
 // whose root sits at depth depth0 of an enclosing tree (the depth cap counts
 // from the enclosing root).  When n_parent / leaf_parent are given, every new
