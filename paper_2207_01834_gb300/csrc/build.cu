@@ -4,14 +4,16 @@
 // Level-synchronous top-down build.  At every level each active segment (a
 // contiguous range of the point array holding one node's points) is
 // classified as a leaf or split at the midpoint of its tight bounding box in
-// its widest dimension.  All points of split segments are then partitioned
-// stably in one pass: a device-wide exclusive scan of the "goes left" flags
-// gives every point its destination, because each segment is contiguous
-// (left rank = scan[i] - scan[segment start]).  The same pass reduces the two
-// children's tight boxes with warp-aggregated integer atomics on an
-// order-preserving float encoding.  The node that a segment becomes is
+// its widest dimension.  All points of split segments are then partitioned:
+// a segmented scan of the "goes left" flags (restarting at every segment
+// start) gives each point its rank among the left-going points of its
+// segment; left points keep their order at the front of the segment, right
+// points fill it from the back.  The same pass reduces the two children's
+// tight boxes (per tile in shared memory, then integer atomics on an
+// order-preserving float encoding).  The node that a segment becomes is
 // numbered by a scan over the level's split flags, so the layout is
-// deterministic.
+// deterministic.  Segments small enough for one block's shared memory are
+// finished there (cta_build_smem.cuh).
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -25,7 +27,6 @@ namespace pg {
 namespace {
 
 constexpr int BT = 256;
-constexpr int kSmemChildren = 64;   // children reduced in shared memory first
 
 struct Segs {
     int *start, *end, *parent, *side, *depth, *lo, *hi;
@@ -91,119 +92,113 @@ __global__ void __launch_bounds__(BT) k_pack(const float *__restrict__ src, cons
 // live values here and do nothing once the loop is done.
 enum { CTL_S = 0, CTL_NB, CTL_FIN, CTL_DONE, CTL_SCATTERS, CTL_LEVELS, CTL_ROOT_SPLIT, CTL_WORDS };
 
-constexpr int FT_THREADS = 256, FT_ITEMS = 16, FT_TILE = FT_THREADS * FT_ITEMS;
+// Level partition in two passes over tiles of PT_ROWS x PT_THREADS points
+// (position base + row * PT_THREADS + thread):
+//   k_part_tiles  per tile, the number of "goes left" flags after the last
+//                 segment start in the tile (or all of them, with no start),
+//   k_part_carry  segmented exclusive scan of those over the tiles,
+//   k_part        per point, the number r of left-going points before it in
+//                 its segment; left points go to st + r in order, right
+//                 points fill the segment from the end (en - 1 - (i - st - r)),
+//                 so no segment total is needed before the move; the last
+//                 point of a segment writes the two children's ranges.
+// A segment start is a position whose segment differs from the previous one.
+constexpr int PT_THREADS = 256, PT_ROWS = 16, PT_TILE = PT_THREADS * PT_ROWS, PT_WARPS = PT_THREADS / 32;
+constexpr int kBoxSlots = 16;   // children whose boxes a tile reduces in shared memory
 
+// Segmented count: `has` a segment start, `cnt` flags after the last start.
+__device__ __forceinline__ unsigned seg_pack(bool has, int cnt) { return (has ? 0x80000000u : 0u) | (unsigned)cnt; }
+__device__ __forceinline__ unsigned seg_combine(unsigned a, unsigned b) {   // a before b
+    return (b & 0x80000000u) ? (a & 0x80000000u) | b : (a & 0x80000000u) + ((a & 0x7fffffffu) + b);
+}
+
+// Flags and segment starts of one tile; every warp-row's segmented count
+// goes to rowsum[row * PT_WARPS + warp].
 template <int DC>
-__device__ __forceinline__ int point_flag(const float *pf, int64_t i, const int *seg_of, const int *split_flag,
-                                          const int *sdim, const float *sval) {
+__device__ __forceinline__ void tile_flags(int64_t n, int64_t base, const float *pf, const int *seg_of,
+                                           const int *split_flag, const int *sdim, const float *sval,
+                                           unsigned &fbits, unsigned &rbits, int *srow, unsigned *rowsum) {
     constexpr int W = bucket_w(DC);
-    const int s = seg_of[i];
-    if (s < 0 || !split_flag[s]) return 0;
-    return pf[i * 4 * W + sdim[s]] < sval[s];
-}
-
-__device__ __forceinline__ int ft_block_excl(int v, int *wsum, int *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    int x = v;
+    fbits = 0;
+    rbits = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+    for (int j = 0; j < PT_ROWS; ++j) {
+        const int64_t i = base + j * PT_THREADS + threadIdx.x;
+        const bool valid = i < n;
+        const int s = valid ? seg_of[i] : -1;
+        const int sp = (valid && i > 0) ? seg_of[i - 1] : -2;
+        const bool start = valid && s != sp;
+        int f = 0;
+        if (valid && s >= 0 && split_flag[s]) f = pf[i * 4 * W + sdim[s]] < sval[s];
+        srow[j] = s;
+        fbits |= (unsigned)f << j;
+        rbits |= (unsigned)start << j;
+        const unsigned F = __ballot_sync(0xffffffffu, f), R = __ballot_sync(0xffffffffu, start);
+        if (lane == 0) {
+            const unsigned keep = R ? ~((1u << (31 - __clz(R))) - 1u) : 0xffffffffu;
+            rowsum[j * PT_WARPS + warp] = seg_pack(R != 0, __popc(F & keep));
         }
-        if (lane < nw) wsum[lane] = w;
     }
-    __syncthreads();
-    const int off = warp ? wsum[warp - 1] : 0;
-    *total = wsum[nw - 1];
-    __syncthreads();
-    return off + x - v;
-}
-
-// Exclusive scan of the "goes left" flags of all points, flags computed on
-// the fly (reduce / top / down).  Skipped when this level splits nothing.
-template <int DC>
-__global__ void __launch_bounds__(FT_THREADS) k_fscan_reduce(int64_t n, const float4 *__restrict__ P,
-                                                             const int *__restrict__ seg_of,
-                                                             const int *__restrict__ split_flag,
-                                                             const int *__restrict__ sdim,
-                                                             const float *__restrict__ sval,
-                                                             const int *__restrict__ T, int *__restrict__ bsum) {
-    if (*T == 0) return;
-    __shared__ int wsum[32];
-    const float *pf = reinterpret_cast<const float *>(P);
-    const int64_t base = (int64_t)blockIdx.x * FT_TILE;
-    int sum = 0;
-#pragma unroll 4
-    for (int j = threadIdx.x; j < FT_TILE; j += FT_THREADS) {
-        const int64_t i = base + j;
-        if (i < n) sum += point_flag<DC>(pf, i, seg_of, split_flag, sdim, sval);
-    }
-    int tot;
-    ft_block_excl(sum, wsum, &tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) k_fscan_top(int *__restrict__ bsum, int nb, const int *__restrict__ T) {
-    if (*T == 0) return;
-    __shared__ int wsum[32];
-    int carry = 0;
-    for (int base = 0; base < nb; base += 1024) {
-        const int i = base + threadIdx.x;
-        const int v = i < nb ? bsum[i] : 0;
-        int tot;
-        const int ex = ft_block_excl(v, wsum, &tot);
-        if (i < nb) bsum[i] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) bsum[nb] = carry;
 }
 
 template <int DC>
-__global__ void __launch_bounds__(FT_THREADS) k_fscan_down(int64_t n, const float4 *__restrict__ P,
+__global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const float4 *__restrict__ P,
                                                            const int *__restrict__ seg_of,
                                                            const int *__restrict__ split_flag,
                                                            const int *__restrict__ sdim,
                                                            const float *__restrict__ sval,
-                                                           const int *__restrict__ T, const int *__restrict__ bsum,
-                                                           int nb, int *__restrict__ pre) {
+                                                           const int *__restrict__ T, unsigned *__restrict__ tsum) {
     if (*T == 0) return;
-    __shared__ int tile[FT_TILE];
-    __shared__ int wsum[32];
-    const float *pf = reinterpret_cast<const float *>(P);
-    const int64_t base = (int64_t)blockIdx.x * FT_TILE;
-    for (int j = threadIdx.x; j < FT_TILE; j += FT_THREADS) {
-        const int64_t i = base + j;
-        tile[j] = i < n ? point_flag<DC>(pf, i, seg_of, split_flag, sdim, sval) : 0;
-    }
+    __shared__ unsigned rowsum[PT_ROWS * PT_WARPS];
+    unsigned fbits, rbits;
+    int srow[PT_ROWS];
+    tile_flags<DC>(n, (int64_t)blockIdx.x * PT_TILE, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim,
+                   sval, fbits, rbits, srow, rowsum);
     __syncthreads();
-    int loc[FT_ITEMS];
-    int sum = 0;
-#pragma unroll
-    for (int j = 0; j < FT_ITEMS; ++j) {
-        loc[j] = sum;
-        sum += tile[threadIdx.x * FT_ITEMS + j];
+    if (threadIdx.x == 0) {
+        unsigned a = 0;
+        for (int e = 0; e < PT_ROWS * PT_WARPS; ++e) a = seg_combine(a, rowsum[e]);
+        tsum[blockIdx.x] = a;
     }
-    int tot;
-    const int ex = ft_block_excl(sum, wsum, &tot);
-    const int off = bsum[blockIdx.x] + ex;
+}
+
+// Segmented exclusive scan over the tiles (one block).
+__global__ void __launch_bounds__(1024) k_part_carry(unsigned *__restrict__ tsum, int ntiles, const int *__restrict__ T) {
+    if (*T == 0) return;
+    __shared__ unsigned wtot[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned carry = 0;
+    for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+        const int t = b0 + threadIdx.x;
+        const unsigned v = t < ntiles ? tsum[t] : 0u;
+        unsigned x = v;
 #pragma unroll
-    for (int j = 0; j < FT_ITEMS; ++j) tile[threadIdx.x * FT_ITEMS + j] = off + loc[j];
-    __syncthreads();
-    for (int j = threadIdx.x; j < FT_TILE; j += FT_THREADS) {
-        const int64_t i = base + j;
-        if (i < n) pre[i] = tile[j];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x = seg_combine(y, x);
+        }
+        if (lane == 31) wtot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned w = wtot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w = seg_combine(y, w);
+            }
+            wtot[lane] = w;
+        }
+        __syncthreads();
+        // exclusive: everything before this tile
+        unsigned ex = __shfl_up_sync(0xffffffffu, x, 1);
+        if (lane == 0) ex = 0u;
+        if (warp > 0) ex = seg_combine(wtot[warp - 1], ex);
+        ex = seg_combine(carry, ex);
+        if (t < ntiles) tsum[t] = ex;
+        carry = seg_combine(carry, wtot[31]);
+        __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) pre[n] = bsum[nb];
 }
 
 // End of a level: advance the control block (one thread).
@@ -339,71 +334,87 @@ __global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__rest
     }
 }
 
+// Move every point of a split segment to its child range (see k_part_tiles)
+// and reduce the children's tight boxes: per tile in shared memory (children
+// of a tile are few and consecutive), then one global atomic per child and
+// dimension; a child that finds its slot taken goes straight to global memory.
 template <int DC>
-__global__ void __launch_bounds__(BT) k_flag(int64_t n, const float4 *__restrict__ P,
-                                             const int *__restrict__ seg_of, const int *__restrict__ split_flag,
-                                             const int *__restrict__ sdim, const float *__restrict__ sval,
-                                             int *__restrict__ flag) {
+__global__ void __launch_bounds__(PT_THREADS) k_part(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
+                                                     const int *__restrict__ seg_of, int *__restrict__ seg_of_nx,
+                                                     const int *__restrict__ start, const int *__restrict__ end,
+                                                     const int *__restrict__ split_flag,
+                                                     const int *__restrict__ split_rank,
+                                                     const int *__restrict__ sdim, const float *__restrict__ sval,
+                                                     const unsigned *__restrict__ tcarry, int *__restrict__ nx_start,
+                                                     int *__restrict__ nx_end, int *__restrict__ nx_lo,
+                                                     int *__restrict__ nx_hi, const int *__restrict__ T) {
     constexpr int W = bucket_w(DC);
-    const float *pf = reinterpret_cast<const float *>(P);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int s = seg_of[i];
-        int f = 0;
-        if (s >= 0 && split_flag[s]) f = pf[i * 4 * W + sdim[s]] < sval[s];
-        flag[i] = f;
+    if (*T == 0) return;
+    __shared__ unsigned rowsum[PT_ROWS * PT_WARPS];
+    __shared__ int tag[kBoxSlots];
+    __shared__ int b_lo[kBoxSlots * DC], b_hi[kBoxSlots * DC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * PT_TILE;
+    if (threadIdx.x < kBoxSlots) tag[threadIdx.x] = -1;
+    for (int x = threadIdx.x; x < kBoxSlots * DC; x += PT_THREADS) {
+        b_lo[x] = 0x7f800000;
+        b_hi[x] = (int)0x807fffffu;
     }
-}
-
-// Stable partition of every split segment + child tight boxes.
-template <int DC>
-__global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
-                                                const int *__restrict__ seg_of, int *__restrict__ seg_of_nx,
-                                                const int *__restrict__ start, const int *__restrict__ end,
-                                                const int *__restrict__ split_flag,
-                                                const int *__restrict__ split_rank, const int *__restrict__ pre,
-                                                int *__restrict__ nx_start, int *__restrict__ nx_end,
-                                                int *__restrict__ nx_lo, int *__restrict__ nx_hi,
-                                                const int *__restrict__ split_total) {
-    constexpr int W = bucket_w(DC);
-    const int lane = threadIdx.x & 31;
-    const int nchild = 2 * *split_total;
-    if (nchild == 0) return;
-    // With few children (top levels) every block first reduces the boxes in
-    // shared memory and then adds one global atomic per child and dimension;
-    // otherwise warps go straight to global memory.
-    __shared__ int s_lo[kSmemChildren * DC], s_hi[kSmemChildren * DC];
-    const bool use_smem = nchild <= kSmemChildren;
-    if (use_smem) {
-        for (int x = threadIdx.x; x < nchild * DC; x += blockDim.x) {
-            s_lo[x] = 0x7f800000;
-            s_hi[x] = (int)0x807fffffu;
+    unsigned fbits, rbits;
+    int srow[PT_ROWS];
+    tile_flags<DC>(n, base, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval, fbits, rbits, srow,
+                   rowsum);
+    __syncthreads();
+    // segmented exclusive scan of the tile's warp-rows (warp 0, 4 per lane)
+    if (warp == 0) {
+        constexpr int PER = PT_ROWS * PT_WARPS / 32;
+        unsigned loc = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) loc = seg_combine(loc, rowsum[lane * PER + k]);
+        unsigned x = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x = seg_combine(y, x);
         }
-        __syncthreads();
+        unsigned in = __shfl_up_sync(0xffffffffu, x, 1);
+        if (lane == 0) in = 0u;
+        in = seg_combine(tcarry[blockIdx.x], in);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const unsigned e = rowsum[lane * PER + k];
+            rowsum[lane * PER + k] = in;
+            in = seg_combine(in, e);
+        }
     }
-    int *box_lo = use_smem ? s_lo : nx_lo;
-    int *box_hi = use_smem ? s_hi : nx_hi;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t i = base + threadIdx.x;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < PT_ROWS; ++j) {
+        const int64_t i = base + j * PT_THREADS + threadIdx.x;
         const bool valid = i < n;
+        const int f = (fbits >> j) & 1u;
+        const unsigned F = __ballot_sync(0xffffffffu, f);
+        const unsigned R = __ballot_sync(0xffffffffu, (rbits >> j) & 1u);
+        const unsigned m = R & (lt | (1u << lane));
+        int r;
+        if (m) r = __popc(F & lt & ~((1u << (31 - __clz(m))) - 1u));
+        else r = (int)(rowsum[j * PT_WARPS + warp] & 0x7fffffffu) + __popc(F & lt);
+        const int s = srow[j];
         int child = -1;
-        int64_t dst = i;
         float4 v[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) v[w] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid) {
 #pragma unroll
             for (int w = 0; w < W; ++w) v[w] = P[i * W + w];
-            const int s = seg_of[i];
+            int64_t dst = i;
             if (s >= 0 && split_flag[s]) {
-                const int st = start[s], en = end[s];
-                const int b0 = pre[st];
-                const int nl = pre[en] - b0;
-                const int r = pre[i] - b0;
-                const int f = pre[i + 1] - pre[i];
-                const int rk = split_rank[s];
+                const int st = start[s], en = end[s], rk = split_rank[s];
                 if (f) { dst = st + r; child = 2 * rk; }
-                else { dst = st + nl + (int)(i - st) - r; child = 2 * rk + 1; }
-                if (i == st) {
+                else { dst = en - 1 - ((int)(i - st) - r); child = 2 * rk + 1; }
+                if (i == en - 1) {
+                    const int nl = r + f;
                     nx_start[2 * rk] = st;
                     nx_end[2 * rk] = st + nl;
                     nx_start[2 * rk + 1] = st + nl;
@@ -413,9 +424,6 @@ __global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restr
 #pragma unroll
             for (int w = 0; w < W; ++w) Q[dst * W + w] = v[w];
             seg_of_nx[dst] = child;
-        } else {
-#pragma unroll
-            for (int w = 0; w < W; ++w) v[w] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const float *cf = reinterpret_cast<const float *>(v);
         unsigned active = __ballot_sync(0xffffffffu, child >= 0);
@@ -424,24 +432,35 @@ __global__ void __launch_bounds__(BT) k_scatter(int64_t n, const float4 *__restr
             const int key = __shfl_sync(0xffffffffu, child, leader);
             const bool mine = child == key;
             const unsigned grp = __ballot_sync(0xffffffffu, mine);
+            int slot = -1;
+            if (lane == leader) {
+                const int t = atomicCAS(&tag[key & (kBoxSlots - 1)], -1, key);
+                if (t == -1 || t == key) slot = key & (kBoxSlots - 1);
+            }
 #pragma unroll
             for (int d = 0; d < DC; ++d) {
                 const int e = f2o(cf[d]);
                 const int a = __reduce_min_sync(0xffffffffu, mine ? e : INT_MAX);
-                const int b = __reduce_max_sync(0xffffffffu, mine ? e : INT_MIN);
+                const int c = __reduce_max_sync(0xffffffffu, mine ? e : INT_MIN);
                 if (lane == leader) {
-                    atomicMin(&box_lo[key * DC + d], a);
-                    atomicMax(&box_hi[key * DC + d], b);
+                    if (slot >= 0) {
+                        atomicMin(&b_lo[slot * DC + d], a);
+                        atomicMax(&b_hi[slot * DC + d], c);
+                    } else {
+                        atomicMin(&nx_lo[key * DC + d], a);
+                        atomicMax(&nx_hi[key * DC + d], c);
+                    }
                 }
             }
             active &= ~grp;
         }
     }
-    if (use_smem) {
-        __syncthreads();
-        for (int x = threadIdx.x; x < nchild * DC; x += blockDim.x) {
-            if (s_lo[x] != 0x7f800000) atomicMin(&nx_lo[x], s_lo[x]);
-            if (s_hi[x] != (int)0x807fffffu) atomicMax(&nx_hi[x], s_hi[x]);
+    __syncthreads();
+    for (int x = threadIdx.x; x < kBoxSlots * DC; x += PT_THREADS) {
+        const int key = tag[x / DC];
+        if (key >= 0) {
+            atomicMin(&nx_lo[key * DC + x % DC], b_lo[x]);
+            atomicMax(&nx_hi[key * DC + x % DC], b_hi[x]);
         }
     }
 }
@@ -540,16 +559,14 @@ pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
 template <int DC>
 pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream_t s, pg_tree *t) {
     constexpr int W = bucket_w(DC);
-    const int grid_pts = std::max(1, std::min(ceil_div_i(n, BT), num_sms() * 8));
     // Split segments hold more than `leaf` points and are disjoint, so a level
     // has at most 2*floor(n/(leaf+1)) segments.
     const int seg_cap = (int)std::max<int64_t>(2, 2 * (n / (leaf + 1)) + 2);
 
-    Scratch sP1, sSeg0, sSeg1, sPre, sSegA, sSegB, sLvl, sBsum, sCtl;
+    Scratch sP1, sSeg0, sSeg1, sSegA, sSegB, sLvl, sBsum, sCtl;
     PG_TRY(sP1.alloc(sizeof(float4) * W * (size_t)n, s));
     PG_TRY(sSeg0.alloc(sizeof(int) * (size_t)n, s));
     PG_TRY(sSeg1.alloc(sizeof(int) * (size_t)n, s));
-    PG_TRY(sPre.alloc(sizeof(int) * (size_t)(n + 1), s));
     const size_t seg_words = (size_t)seg_cap * (5 + 2 * DC);
     PG_TRY(sSegA.alloc(sizeof(int) * seg_words, s));
     PG_TRY(sSegB.alloc(sizeof(int) * seg_words, s));
@@ -561,8 +578,8 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     float *sval = reinterpret_cast<float *>(sdim + seg_cap);
     int *fin_flag = sdim + 2 * seg_cap;
     int *fin_rank = fin_flag + seg_cap;
-    const int ft_tiles = std::max(1, ceil_div_i(n, FT_TILE));
-    PG_TRY(sBsum.alloc(sizeof(int) * (size_t)(ft_tiles + 1), s));
+    const int ntiles = std::max(1, ceil_div_i(n, PT_TILE));
+    PG_TRY(sBsum.alloc(sizeof(unsigned) * (size_t)ntiles, s));
     PG_TRY(sCtl.alloc(sizeof(int) * CTL_WORDS, s));
     int *ctl = sCtl.as<int>();
     // segments handed to the block-scope finisher (disjoint, > leaf points each)
@@ -634,17 +651,15 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
                                      fin_flag, fin_rank, fin, t->parent);
         count_launch();
         const int *T = split_rank + S_max;
-        k_fscan_reduce<DC><<<ft_tiles, FT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<int>());
-        k_fscan_top<<<1, 1024, 0, s>>>(sBsum.as<int>(), ft_tiles, T);
-        k_fscan_down<DC><<<ft_tiles, FT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<int>(),
-                                                          ft_tiles, sPre.as<int>());
-        count_launch();
+        k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<unsigned>());
+        k_part_carry<<<1, 1024, 0, s>>>(sBsum.as<unsigned>(), ntiles, T);
         count_launch();
         count_launch();
         {
             KTimer kt("build_scatter", s);
-            k_scatter<DC><<<grid_pts, BT, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
-                                                  split_rank, sPre.as<int>(), nxt.start, nxt.end, nxt.lo, nxt.hi, T);
+            k_part<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
+                                                     split_rank, sdim, sval, sBsum.as<unsigned>(), nxt.start, nxt.end,
+                                                     nxt.lo, nxt.hi, T);
             count_launch();
         }
         k_level_end<<<1, 1, 0, s>>>(ctl, T, fin_rank + S_max, level);
