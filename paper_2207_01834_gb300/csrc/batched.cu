@@ -15,10 +15,9 @@
 namespace pg {
 
 #define PG_BDECL(DCN)                                                                                      \
-    pg_status batched_launch_dc##DCN(int, const BArgs *, const BWork *, int, int, int *, CloudMeta *, int *,  \
-                                     int *, float4 *, float4 *, float4 *, int *, float *, int2 *, int *,     \
-                                     float *, int, int, int, cudaStream_t);                                \
-    int batched_blocks_per_sm_dc##DCN(int k);
+    int batched_launch_dc##DCN(int, size_t, const BArgs *, const BDev &, cudaStream_t);                    \
+    void batched_pack_dc##DCN(const BArgs *, const CloudMeta *, const int *, int, int, int, float4 *, int *, \
+                              int *, cudaStream_t);
 PG_BDECL(2) PG_BDECL(3) PG_BDECL(4) PG_BDECL(5) PG_BDECL(6) PG_BDECL(7) PG_BDECL(8) PG_BDECL(12) PG_BDECL(16)
 #undef PG_BDECL
 
@@ -164,25 +163,32 @@ __global__ void k_bgrad_heavy(const float *__restrict__ X, const float *__restri
 
 inline int grid_of(int64_t n) { return std::max(1, ceil_div_i(n, BT)); }
 
+constexpr size_t kBatchSmemBudget = 110 * 1024;   // finisher shared memory per block (two blocks per SM)
+
+__global__ void k_bpending(BDev D) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < D.fin_cap && f < D.ctl[D.ctl_fin]) atomicAdd(&D.pending[cloud_of(D.cl_start, D.ncl, D.fin[f])], 1);
+}
+__global__ void k_bready(BDev D, const BArgs *__restrict__ args) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < D.ncl) D.ready[c] = (D.pending[c] == 0 && !args->skip_publish) ? 1 : 0;
+}
+
 struct Plan {
-    int npairs = 0, dim = 0, k = 0, leaf = 0, dc = 2;
+    int npairs = 0, dim = 0, k = 0, leaf = 0, dc = 2, ncl = 0;
     std::vector<long long> a_off, b_off;
-    int64_t Na = 0, Nb = 0, npoints = 0, nnodes = 0, nscratch = 0;
-    int nitems = 0, nbuild = 0, nquery = 0, grid = 0;
+    int64_t Na = 0, Nb = 0, npoints = 0;
+    int nquery = 0, grid = 0, graph_kernels = 0;
+    size_t smem = 0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
-    // device
-    float4 *P = nullptr, *Q = nullptr, *nodes = nullptr;
-    int *sdim = nullptr, *scratch = nullptr, *ready = nullptr, *counter = nullptr, *status = nullptr;
-    float *sval = nullptr, *partial = nullptr;
-    int2 *range = nullptr;
-    CloudMeta *meta = nullptr;
-    BWork *items = nullptr;
+    ForestArgs fa{};
+    BDev D{};
     BArgs *args = nullptr;
+    CloudMeta *meta = nullptr;
+    int *cl_start = nullptr, *cl_end = nullptr, *cl_box = nullptr, *status = nullptr;
     int *first = nullptr;
     float *loss_dev = nullptr;
-    long long *aoff_d = nullptr, *boff_d = nullptr;
-    int *row_pair_a = nullptr, *row_pair_b = nullptr;
     std::vector<void *> owned;
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -207,121 +213,185 @@ pg_status plan_alloc(Plan &pl, T **p, size_t n) {
     return PG_OK;
 }
 
-int blocks_per_sm(int dc, int k) {
-    switch (dc) {
-        case 2: return batched_blocks_per_sm_dc2(k);
-        case 3: return batched_blocks_per_sm_dc3(k);
-        case 4: return batched_blocks_per_sm_dc4(k);
-        case 5: return batched_blocks_per_sm_dc5(k);
-        case 6: return batched_blocks_per_sm_dc6(k);
-        case 7: return batched_blocks_per_sm_dc7(k);
-        case 8: return batched_blocks_per_sm_dc8(k);
-        case 12: return batched_blocks_per_sm_dc12(k);
-        default: return batched_blocks_per_sm_dc16(k);
+#define PG_BSWITCH(dc, CALL)                                                                               \
+    switch (dc) {                                                                                          \
+        case 2: { CALL(2); } break;                                                                        \
+        case 3: { CALL(3); } break;                                                                        \
+        case 4: { CALL(4); } break;                                                                        \
+        case 5: { CALL(5); } break;                                                                        \
+        case 6: { CALL(6); } break;                                                                        \
+        case 7: { CALL(7); } break;                                                                        \
+        case 8: { CALL(8); } break;                                                                        \
+        case 12: { CALL(12); } break;                                                                      \
+        case 16: { CALL(16); } break;                                                                      \
+        default: return fail(PG_EUNSUPPORTED, "dimension class");                                          \
     }
-}
-
-pg_status launch_kernel(Plan &pl, cudaStream_t s) {
-#define PG_BL(D)                                                                                           \
-    case D:                                                                                                \
-        return batched_launch_dc##D(pl.grid, pl.args, pl.items, pl.nitems, pl.nbuild, pl.counter, pl.meta,  \
-                                    pl.ready, pl.status, pl.P, pl.Q, pl.nodes, pl.sdim, pl.sval, pl.range,  \
-                                    pl.scratch, pl.partial, pl.dim, pl.k, pl.leaf, s);
-    switch (pl.dc) {
-        PG_BL(2) PG_BL(3) PG_BL(4) PG_BL(5) PG_BL(6) PG_BL(7) PG_BL(8) PG_BL(12) PG_BL(16)
-        default: return fail(PG_EUNSUPPORTED, "dimension class");
-    }
-#undef PG_BL
-}
 
 // Enqueue one forward pass (everything inside the captured graph).
 pg_status enqueue_forward(Plan &pl, cudaStream_t s) {
-    PG_CUDA(cudaMemsetAsync(pl.ready, 0, sizeof(int) * (size_t)(2 * pl.npairs), s));
-    PG_CUDA(cudaMemsetAsync(pl.counter, 0, sizeof(int), s));
-    PG_CUDA(cudaMemsetAsync(pl.status, 0, sizeof(int), s));
-    PG_TRY(launch_kernel(pl, s));
-    k_pair_loss<<<grid_of(pl.npairs), BT, 0, s>>>(pl.first, pl.partial, pl.npairs, pl.loss_dev);
+    const BDev &D = pl.D;
+    PG_CUDA(cudaMemsetAsync(D.pending, 0, sizeof(int) * (size_t)pl.ncl, s));
+    PG_CUDA(cudaMemsetAsync(D.counter, 0, sizeof(int), s));
+    PG_CUDA(cudaMemsetAsync(D.status, 0, sizeof(int), s));
+    PG_CUDA(cudaMemsetAsync(D.pool_top, 0, sizeof(long long), s));
+#define PG_PACK(DCN)                                                                                       \
+    batched_pack_dc##DCN(pl.args, pl.meta, pl.cl_start, pl.ncl, (int)pl.npoints, pl.dim, pl.fa.P,            \
+                         pl.fa.seg_of, pl.cl_box, s)
+    PG_BSWITCH(pl.dc, PG_PACK)
+#undef PG_PACK
+    PG_TRY(forest_levels(pl.dc, pl.fa, s));
+    k_bpending<<<grid_of(pl.fa.fin_cap), BT, 0, s>>>(D);
+    k_bready<<<grid_of(pl.ncl), BT, 0, s>>>(D, pl.args);
+    count_launch();
+    count_launch();
+    int r = 0;
+#define PG_RUN(DCN) r = batched_launch_dc##DCN(pl.grid, pl.smem, pl.args, D, s)
+    PG_BSWITCH(pl.dc, PG_RUN)
+#undef PG_RUN
+    if (r < 0) return fail(PG_EINVAL, "k out of range");
+    PG_TRY(check_launch("batched persistent kernel"));
+    k_pair_loss<<<grid_of(pl.npairs), BT, 0, s>>>(pl.first, D.partial, pl.npairs, pl.loss_dev);
     count_launch();
     return check_launch("batched loss");
 }
 
 pg_status make_plan(Plan &pl) {
-    const int np = pl.npairs;
-    const int W = bucket_w(pl.dc), NWv = node_w(pl.dc);
-    (void)W;
-    (void)NWv;
-    std::vector<CloudMeta> meta(2 * np);
-    int64_t pos = 0, node = 0, scr = 0;
-    std::vector<std::pair<int, int>> order;   // (size, cloud)
+    const int np = pl.npairs, dc = pl.dc;
+    pl.ncl = 2 * np;
+    std::vector<CloudMeta> meta(pl.ncl);
+    std::vector<int> cl_start(pl.ncl), cl_end(pl.ncl);
+    int64_t pos = 0, max_n = 1;
     for (int i = 0; i < np; ++i) {
         for (int side = 0; side < 2; ++side) {
             const int c = 2 * i + side;
             const std::vector<long long> &off = side == 0 ? pl.a_off : pl.b_off;
             const int64_t n = off[i + 1] - off[i];
-            CloudMeta &m = meta[c];
-            memset(&m, 0, sizeof(m));
-            m.off = (int)pos;
-            m.n = (int)n;
-            m.node_base = (int)node;
-            m.row0 = (int)off[i];
-            m.src = side;
-            m.scratch_off = scr;
-            // 8-entry alignment keeps every cloud's buckets and nodes on their
-            // own 128-byte lines (readers never see another cloud's stale line)
+            meta[c] = CloudMeta{(int)pos, (int)n, (int)off[i], side};
+            cl_start[c] = (int)pos;
+            cl_end[c] = (int)(pos + n);
+            max_n = std::max(max_n, n);
+            // 8-entry alignment keeps every cloud's buckets and finisher node
+            // slots on their own 128-byte lines: a block never caches a line
+            // that another cloud's finisher is still writing
             pos += (n + 7) / 8 * 8;
-            node += (std::max<int64_t>(n - 1, 1) + 7) / 8 * 8;
-            scr += (cta_scratch_words(n, pl.leaf, pl.dc) + 31) / 32 * 32;
-            order.push_back({(int)n, c});
         }
     }
-    if (pos >= ((int64_t)1 << 31) || node >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "batched: too many points");
     pl.npoints = pos;
-    pl.nnodes = node;
-    pl.nscratch = scr;
-    std::sort(order.begin(), order.end(), [](auto &x, auto &y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
+    // query work items: chunks of BATCH_NT points per (pair, direction)
     std::vector<BWork> items;
-    for (auto &o : order) items.push_back({0, o.second, 0, 0});
-    pl.nbuild = (int)items.size();
     std::vector<int> first(np + 1, 0);
     for (int i = 0; i < np; ++i) {
-        first[i] = (int)items.size() - pl.nbuild;
+        first[i] = (int)items.size();
         for (int dir = 0; dir < 2; ++dir) {
             const int n = meta[2 * i + dir].n;
-            for (int st = 0; st < n; st += BATCH_NT) items.push_back({1, i, dir, st});
+            for (int st = 0; st < n; st += BATCH_NT) items.push_back({i, dir, st, 0});
         }
     }
-    first[np] = (int)items.size() - pl.nbuild;
-    pl.nitems = (int)items.size();
-    pl.nquery = pl.nitems - pl.nbuild;
-    const int W4 = bucket_w(pl.dc);
-    PG_TRY(plan_alloc(pl, &pl.P, (size_t)pl.npoints * W4));
-    PG_TRY(plan_alloc(pl, &pl.Q, (size_t)pl.npoints * W4));
-    PG_TRY(plan_alloc(pl, &pl.nodes, (size_t)pl.nnodes * node_w(pl.dc)));
-    PG_TRY(plan_alloc(pl, &pl.sdim, (size_t)pl.nnodes));
-    PG_TRY(plan_alloc(pl, &pl.sval, (size_t)pl.nnodes));
-    PG_TRY(plan_alloc(pl, &pl.range, (size_t)pl.nnodes));
-    PG_TRY(plan_alloc(pl, &pl.scratch, (size_t)pl.nscratch));
-    PG_TRY(plan_alloc(pl, &pl.ready, (size_t)(2 * np)));
-    PG_TRY(plan_alloc(pl, &pl.counter, 1));
-    PG_TRY(plan_alloc(pl, &pl.status, 1));
-    PG_TRY(plan_alloc(pl, &pl.partial, (size_t)pl.nquery));
-    PG_TRY(plan_alloc(pl, &pl.meta, (size_t)(2 * np)));
-    PG_TRY(plan_alloc(pl, &pl.items, (size_t)pl.nitems));
+    first[np] = (int)items.size();
+    pl.nquery = (int)items.size();
+    // forest levels: enough for balanced splits of the largest cloud down to
+    // one block's shared memory, plus a margin for clustered clouds
+    const int ns = smem_build_points(dc, pl.leaf, kBatchSmemBudget);
+    const int sc = smem_seg_cap(ns, pl.leaf);
+    int levels = 1;
+    while (((int64_t)ns << (levels - 1)) < max_n && levels < PG_DEPTH_CAP) ++levels;
+    levels = std::min(levels + 6, PG_DEPTH_CAP + 1);
+    ForestArgs &fa = pl.fa;
+    fa.n = pl.npoints;
+    fa.ntrees = pl.ncl;
+    fa.leaf = pl.leaf;
+    fa.fin_max = ns;
+    fa.levels = levels;
+    // level splits hold more than ns points each (at most npoints/(ns+1) per level)
+    fa.seg_cap = (int)std::max<int64_t>(pl.ncl, 2 * (pl.npoints / (ns + 1)) + 2);
+    fa.fin_cap = (int)(pl.npoints / (pl.leaf + 1) + pl.ncl + 1);
+    fa.node_off = (int)pos;   // finisher segments own the slots of their positions
+    const int64_t nnodes = pos + (int64_t)levels * (pl.npoints / (ns + 1) + 1) + 64;
+    if (nnodes >= ((int64_t)1 << 31) || pl.npoints >= ((int64_t)1 << 31) - 64)
+        return fail(PG_EINVAL, "batched: too many points");
+    const int W4 = bucket_w(dc);
+    PG_TRY(plan_alloc(pl, &fa.P, (size_t)pl.npoints * W4));
+    PG_TRY(plan_alloc(pl, &fa.Q, (size_t)pl.npoints * W4));
+    PG_TRY(plan_alloc(pl, &fa.seg_of, (size_t)pl.npoints));
+    PG_TRY(plan_alloc(pl, &fa.seg_of_nx, (size_t)pl.npoints));
+    PG_TRY(plan_alloc(pl, &fa.nodes, (size_t)nnodes * node_w(dc)));
+    PG_TRY(plan_alloc(pl, &fa.n_sdim, (size_t)nnodes));
+    PG_TRY(plan_alloc(pl, &fa.n_sval, (size_t)nnodes));
+    PG_TRY(plan_alloc(pl, &fa.n_range, (size_t)nnodes));
+    PG_TRY(plan_alloc(pl, &fa.n_parent, (size_t)nnodes));
+    PG_TRY(plan_alloc(pl, &fa.roots, (size_t)(2 * pl.ncl)));
+    int *fw = nullptr;
+    PG_TRY(plan_alloc(pl, &fw, (size_t)forest_words(dc, fa.seg_cap, fa.fin_cap, fa.n)));
+    forest_carve(fa, fw, dc);
+    PG_TRY(plan_alloc(pl, &pl.cl_start, (size_t)pl.ncl));
+    PG_TRY(plan_alloc(pl, &pl.cl_end, (size_t)pl.ncl));
+    PG_TRY(plan_alloc(pl, &pl.cl_box, (size_t)pl.ncl * 2 * dc));
+    fa.t_start = pl.cl_start;
+    fa.t_end = pl.cl_end;
+    fa.t_box = pl.cl_box;
+    PG_TRY(plan_alloc(pl, &pl.meta, (size_t)pl.ncl));
     PG_TRY(plan_alloc(pl, &pl.args, 1));
     PG_TRY(plan_alloc(pl, &pl.first, (size_t)(np + 1)));
     PG_TRY(plan_alloc(pl, &pl.loss_dev, (size_t)np));
-    PG_TRY(plan_alloc(pl, &pl.aoff_d, (size_t)(np + 1)));
-    PG_TRY(plan_alloc(pl, &pl.boff_d, (size_t)(np + 1)));
+    BDev &D = pl.D;
+    BWork *items_d = nullptr;
+    PG_TRY(plan_alloc(pl, &items_d, (size_t)pl.nquery));
+    D.items = items_d;
+    D.nquery = pl.nquery;
+    PG_TRY(plan_alloc(pl, &D.counter, 1));
+    PG_TRY(plan_alloc(pl, &D.status, 1));
+    pl.status = D.status;
+    D.ctl = fa.ctl;
+    const ForestCtl fcw = forest_ctl();
+    D.ctl_nb = fcw.nb;
+    D.ctl_fin = fcw.fin;
+    D.ctl_scat = fcw.scatters;
+    D.fin = fa.fin;
+    D.fin_cap = fa.fin_cap;
+    D.meta = pl.meta;
+    D.cl_start = pl.cl_start;
+    D.cl_box = pl.cl_box;
+    D.ncl = pl.ncl;
+    D.roots = fa.roots;
+    PG_TRY(plan_alloc(pl, &D.pending, (size_t)pl.ncl));
+    PG_TRY(plan_alloc(pl, &D.ready, (size_t)pl.ncl));
+    D.P = fa.P;
+    D.Q = fa.Q;
+    D.nodes = fa.nodes;
+    D.sdim = fa.n_sdim;
+    D.sval = fa.n_sval;
+    D.range = fa.n_range;
+    D.parent = fa.n_parent;
+    // scratch for finisher segments above ns points (only after the last
+    // level): the sizes are disjoint parts of npoints, each above ns
+    D.pool_cap = cta_scratch_words(pl.npoints, pl.leaf, dc) +
+                 (pl.npoints / (ns + 1) + 1) * (cta_scratch_words(0, pl.leaf, dc) + 64);
+    PG_TRY(plan_alloc(pl, &D.pool, (size_t)D.pool_cap));
+    PG_TRY(plan_alloc(pl, &D.pool_top, 1));
+    PG_TRY(plan_alloc(pl, &D.partial, (size_t)pl.nquery));
+    D.dim = pl.dim;
+    D.k = pl.k;
+    D.leaf = pl.leaf;
+    D.ns = ns;
+    D.sc = sc;
+    pl.smem = smem_build_bytes(ns, sc, dc);
     PG_CUDA(cudaMemcpy(pl.meta, meta.data(), sizeof(CloudMeta) * meta.size(), cudaMemcpyHostToDevice));
-    PG_CUDA(cudaMemcpy(pl.items, items.data(), sizeof(BWork) * items.size(), cudaMemcpyHostToDevice));
+    PG_CUDA(cudaMemcpy(pl.cl_start, cl_start.data(), sizeof(int) * cl_start.size(), cudaMemcpyHostToDevice));
+    PG_CUDA(cudaMemcpy(pl.cl_end, cl_end.data(), sizeof(int) * cl_end.size(), cudaMemcpyHostToDevice));
+    PG_CUDA(cudaMemcpy(items_d, items.data(), sizeof(BWork) * items.size(), cudaMemcpyHostToDevice));
     PG_CUDA(cudaMemcpy(pl.first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice));
-    PG_CUDA(cudaMemcpy(pl.aoff_d, pl.a_off.data(), sizeof(long long) * (np + 1), cudaMemcpyHostToDevice));
-    PG_CUDA(cudaMemcpy(pl.boff_d, pl.b_off.data(), sizeof(long long) * (np + 1), cudaMemcpyHostToDevice));
-    pl.grid = num_sms() * blocks_per_sm(pl.dc, pl.k);
+    int per_sm = 0;
+#define PG_OCC(DCN) per_sm = batched_launch_dc##DCN(0, pl.smem, pl.args, D, nullptr)
+    PG_BSWITCH(dc, PG_OCC)
+#undef PG_OCC
+    if (per_sm <= 0) return fail(PG_EINVAL, "k out of range");
+    pl.grid = num_sms() * per_sm;
     // capture the forward sequence once; calls only refresh the argument block
     PG_CUDA(cudaStreamCreateWithFlags(&pl.cap, cudaStreamNonBlocking));
     PG_CUDA(cudaStreamBeginCapture(pl.cap, cudaStreamCaptureModeThreadLocal));
+    const uint64_t before = pg_launch_count();
     pg_status st = enqueue_forward(pl, pl.cap);
+    pl.graph_kernels = (int)(pg_launch_count() - before);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(pl.cap, &graph);
     if (st != PG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
@@ -388,13 +458,13 @@ extern "C" pg_status pg_batched_chamfer(const float *a, const int64_t *a_off, co
     BArgs args{a, b, idx_ab, idx_ba, dist_ab, dist_ba, g_wait_limit, g_skip_publish};
     PG_CUDA(cudaMemcpyAsync(pl->args, &args, sizeof(args), cudaMemcpyHostToDevice, s));
     PG_CUDA(cudaGraphLaunch(pl->exec, s));
-    count_launch();   // persistent kernel
-    count_launch();   // per-pair loss sums
+    for (int i = 0; i < pl->graph_kernels; ++i) count_launch();   // the graph's kernel nodes
     PG_CUDA(cudaMemcpyAsync(loss, pl->loss_dev, sizeof(float) * npairs, cudaMemcpyDeviceToDevice, s));
     int st = 0;
     PG_CUDA(cudaMemcpyAsync(&st, pl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
-    if (st) return fail(PG_ETIMEOUT, "pg_batched_chamfer: a query waited too long for a tree");
+    if (st == 1) return fail(PG_ETIMEOUT, "pg_batched_chamfer: a query waited too long for a tree");
+    // st == 2: a finisher ran out of scratch and kept one leaf (results stay exact)
     return PG_OK;
 }
 

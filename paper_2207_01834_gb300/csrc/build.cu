@@ -21,6 +21,7 @@
 
 #include "cta_build_smem.cuh"
 #include "internal.h"
+#include "sort.h"
 
 namespace pg {
 
@@ -268,7 +269,7 @@ __global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__rest
                        int2 *__restrict__ n_range, int *__restrict__ nx_parent, int *__restrict__ nx_side,
                        int *__restrict__ nx_depth, int *__restrict__ nx_lo, int *__restrict__ nx_hi,
                        const int *__restrict__ fin_flag, const int *__restrict__ fin_rank, Segs fin,
-                       int *__restrict__ n_parent) {
+                       int *__restrict__ n_parent, int *__restrict__ roots, int fin_link) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S_max || ctl[CTL_DONE] || s >= ctl[CTL_S]) return;
     const int node_base = ctl[CTL_NB], fin_base = ctl[CTL_FIN];
@@ -297,11 +298,23 @@ __global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__rest
                 rec[c * 2 * DC + d] = o2f(lo[s * DC + d]);
                 rec[c * 2 * DC + DC + d] = o2f(hi[s * DC + d]);
             }
+            if (fin_link) {   // forest: the finisher puts the subtree root in slot en - 1
+                int *ri = reinterpret_cast<int *>(rec + 4 * DC);
+                ri[2 * c] = st + size - 1;
+                ri[2 * c + 1] = 0;
+            }
+        } else if (p < -1) {
+            roots[2 * (-p - 2)] = st + size - 1;
+            roots[2 * (-p - 2) + 1] = 0;
         }
         return;
     }
     const int code = p >= 0 ? 2 * p + side[s] : -1;   // where this segment hangs
     if (split) n_parent[node] = code;
+    if (p < -1) {   // root of tree -p-2 of a forest
+        roots[2 * (-p - 2)] = split ? node : st;
+        roots[2 * (-p - 2) + 1] = split ? 0 : size;
+    }
     if (p >= 0) {
         float *rec = rec_of(nodes, p, DC);
         const int c = side[s];
@@ -648,7 +661,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         k_link<DC><<<gs, BT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo,
                                      cur.hi, split_flag, split_rank, sdim, sval, t->nodes, t->split_dim,
                                      t->split_val, t->node_range, nxt.parent, nxt.side, nxt.depth, nxt.lo, nxt.hi,
-                                     fin_flag, fin_rank, fin, t->parent);
+                                     fin_flag, fin_rank, fin, t->parent, nullptr, 0);
         count_launch();
         const int *T = split_rank + S_max;
         k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<unsigned>());
@@ -722,6 +735,93 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     return PG_OK;
 }
 
+// ---------------------------------------------------------------- forest
+// Many independent trees at once: level 0 holds one root segment per tree
+// (parent code -(t+2) for tree t), and the same level kernels split all of
+// them together.  A fixed number of levels is enqueued (no host wait, so the
+// sequence can be captured in a graph); at the last level every segment that
+// could still split is handed to the finisher list instead.  Finisher
+// segment [st, en) owns node slots [st, en) and puts its root (always an
+// internal node: the segment could split) in slot en - 1, so its parent is
+// linked here; level nodes are numbered from node_off on.
+
+template <int DC>
+__global__ void k_forest_init(int ntrees, const int *__restrict__ t_start, const int *__restrict__ t_end,
+                              const int *__restrict__ t_box, int node_off, Segs cur, int *__restrict__ ctl) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        for (int w = 0; w < CTL_WORDS; ++w) ctl[w] = 0;
+        ctl[CTL_S] = ntrees;
+        ctl[CTL_NB] = node_off;
+    }
+    if (t >= ntrees) return;
+    cur.start[t] = t_start[t];
+    cur.end[t] = t_end[t];
+    cur.parent[t] = -(t + 2);
+    cur.side[t] = 0;
+    cur.depth[t] = 0;
+#pragma unroll
+    for (int d = 0; d < DC; ++d) {
+        cur.lo[t * DC + d] = t_box[t * 2 * DC + d];
+        cur.hi[t * DC + d] = t_box[t * 2 * DC + DC + d];
+    }
+}
+
+template <int DC>
+pg_status forest_levels_impl(const ForestArgs &fa, cudaStream_t s) {
+    const int seg_cap = fa.seg_cap, fin_cap = fa.fin_cap;
+    auto carve = [&](int *b, int cap) {
+        Segs g;
+        g.start = b; g.end = b + cap; g.parent = b + 2 * cap; g.side = b + 3 * cap;
+        g.depth = b + 4 * cap; g.lo = b + 5 * cap; g.hi = b + (5 + DC) * cap;
+        return g;
+    };
+    Segs cur = carve(fa.seg_a, seg_cap), nxt = carve(fa.seg_b, seg_cap), fin = carve(fa.fin, fin_cap);
+    int *split_flag = fa.lvl;
+    int *split_rank = split_flag + seg_cap;
+    int *sdim = split_rank + seg_cap + 1;
+    float *sval = reinterpret_cast<float *>(sdim + seg_cap);
+    int *fin_flag = sdim + 2 * seg_cap;
+    int *fin_rank = fin_flag + seg_cap;
+    float4 *P = fa.P, *Q = fa.Q;
+    int *seg_of = fa.seg_of, *seg_of_nx = fa.seg_of_nx;
+    const int ntiles = std::max(1, ceil_div_i(fa.n, PT_TILE));
+    k_forest_init<DC><<<ceil_div_i(fa.ntrees, BT), BT, 0, s>>>(fa.ntrees, fa.t_start, fa.t_end, fa.t_box,
+                                                               fa.node_off, cur, fa.ctl);
+    count_launch();
+    for (int level = 0; level < fa.levels; ++level) {
+        const int S_max = (int)std::min<int64_t>((int64_t)fa.ntrees << std::min(level, 30), seg_cap);
+        const int gs = ceil_div_i(S_max, BT);
+        const int thr = level == fa.levels - 1 ? INT_MAX : fa.fin_max;
+        k_classify<DC><<<gs, BT, 0, s>>>(S_max, fa.ctl, cur.start, cur.end, cur.depth, cur.lo, cur.hi, fa.leaf,
+                                         PG_DEPTH_CAP, thr, split_flag, fin_flag, sdim, sval);
+        count_launch();
+        PG_TRY(exclusive_scan_ws(split_flag, split_rank, S_max, fa.scan_ws, s));
+        PG_TRY(exclusive_scan_ws(fin_flag, fin_rank, S_max, fa.scan_ws, s));
+        k_link<DC><<<gs, BT, 0, s>>>(S_max, fa.ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo,
+                                     cur.hi, split_flag, split_rank, sdim, sval, fa.nodes, fa.n_sdim, fa.n_sval,
+                                     fa.n_range, nxt.parent, nxt.side, nxt.depth, nxt.lo, nxt.hi, fin_flag,
+                                     fin_rank, fin, fa.n_parent, fa.roots, 1);
+        count_launch();
+        const int *T = split_rank + S_max;
+        k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(fa.n, P, seg_of, split_flag, sdim, sval, T, fa.tiles);
+        k_part_carry<<<1, 1024, 0, s>>>(fa.tiles, ntiles, T);
+        k_part<DC><<<ntiles, PT_THREADS, 0, s>>>(fa.n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
+                                                 split_rank, sdim, sval, fa.tiles, nxt.start, nxt.end, nxt.lo,
+                                                 nxt.hi, T);
+        k_level_end<<<1, 1, 0, s>>>(fa.ctl, T, fin_rank + S_max, level);
+        count_launch();
+        count_launch();
+        count_launch();
+        count_launch();
+        PG_TRY(check_launch("forest level"));
+        std::swap(P, Q);
+        std::swap(seg_of, seg_of_nx);
+        std::swap(cur, nxt);
+    }
+    return PG_OK;
+}
+
 template <int DC>
 pg_status pack_impl(const float *src, const int32_t *rows, const int32_t *ids, int64_t n, int dim, float4 *out,
                     int *box, cudaStream_t s) {
@@ -736,6 +836,40 @@ pg_status pack_impl(const float *src, const int32_t *rows, const int32_t *ids, i
 }
 
 }  // namespace
+
+int64_t forest_words(int dc, int seg_cap, int fin_cap, int64_t n) {
+    const int64_t ntiles = std::max<int64_t>(1, (n + PT_TILE - 1) / PT_TILE);
+    return 2 * (int64_t)seg_cap * (5 + 2 * dc) + 6 * (int64_t)seg_cap + 2 + (int64_t)fin_cap * (5 + 2 * dc) + ntiles +
+           CTL_WORDS + scan_ws_words(seg_cap) + 64;
+}
+
+void forest_carve(ForestArgs &fa, int *words, int dc) {
+    int *p = words;
+    fa.seg_a = p; p += (size_t)fa.seg_cap * (5 + 2 * dc);
+    fa.seg_b = p; p += (size_t)fa.seg_cap * (5 + 2 * dc);
+    fa.lvl = p; p += 6 * (size_t)fa.seg_cap + 2;
+    fa.fin = p; p += (size_t)fa.fin_cap * (5 + 2 * dc);
+    fa.tiles = reinterpret_cast<unsigned *>(p); p += std::max<int64_t>(1, (fa.n + PT_TILE - 1) / PT_TILE);
+    fa.ctl = p; p += CTL_WORDS;
+    fa.scan_ws = p;
+}
+
+ForestCtl forest_ctl() { return ForestCtl{CTL_NB, CTL_FIN, CTL_SCATTERS}; }
+
+pg_status forest_levels(int dc, const ForestArgs &fa, cudaStream_t s) {
+    switch (dc) {
+        case 2: return forest_levels_impl<2>(fa, s);
+        case 3: return forest_levels_impl<3>(fa, s);
+        case 4: return forest_levels_impl<4>(fa, s);
+        case 5: return forest_levels_impl<5>(fa, s);
+        case 6: return forest_levels_impl<6>(fa, s);
+        case 7: return forest_levels_impl<7>(fa, s);
+        case 8: return forest_levels_impl<8>(fa, s);
+        case 12: return forest_levels_impl<12>(fa, s);
+        case 16: return forest_levels_impl<16>(fa, s);
+        default: return fail(PG_EUNSUPPORTED, "dimension class");
+    }
+}
 
 #define PG_DC_SWITCH(dc, CALL)                                   \
     switch (dc) {                                                \

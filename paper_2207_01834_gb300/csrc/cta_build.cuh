@@ -107,13 +107,15 @@ __device__ int cta_excl_scan(const int *in, int *out, int L, int *s_w) {
 // Q is a ping-pong buffer addressed by the same positions.  Nodes are written
 // to node indices node_base .. node_base + (s1 - s0 - 2) (at most n-1 nodes).
 // root_lo/root_hi: the range's tight box as order-preserving ints.
+// root_slot >= 0: the root, if it splits, goes to that node slot instead.
 // Returns the tree's root reference and node count (valid in thread 0 and,
 // after the final barrier, in every thread).
 template <int DC, int NT>
 __device__ CtaTree cta_build_tree(float4 *P, float4 *Q, int s0, int s1, const int *root_lo, const int *root_hi,
                                   int *scratch, int leaf, int node_base, float4 *nodes, int *n_sdim,
                                   float *n_sval, int2 *n_range, int *s_w, int depth0 = 0,
-                                  int *n_parent = nullptr, int *leaf_parent = nullptr, int root_code = -1) {
+                                  int *n_parent = nullptr, int *leaf_parent = nullptr, int root_code = -1,
+                                  int root_slot = -1) {
     constexpr int W = bucket_w(DC);
     const int n = s1 - s0;
     CtaScratch<DC> sc;
@@ -169,7 +171,7 @@ __device__ CtaTree cta_build_tree(float4 *P, float4 *Q, int s0, int s1, const in
         for (int s = threadIdx.x; s < S; s += NT) {
             const int st = cur.start[s], size = cur.end[s] - st;
             const bool split = sc.split[s] != 0;
-            const int node = node_base + used + sc.rank[s];
+            const int node = (level == 0 && root_slot >= 0) ? root_slot : node_base + used + sc.rank[s];
             const int p = cur.parent[s];
             // where this segment hangs in the whole tree (parent node, side)
             const int code = p >= 0 ? 2 * p + cur.side[s] : root_code;

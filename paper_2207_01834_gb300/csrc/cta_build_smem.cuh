@@ -121,11 +121,14 @@ __device__ __forceinline__ void warp_popc_scan(const uint32_t *w, int *pre, int 
 // Build the tree of bucket entries P[s0, s1) (packed, any order; at most ns
 // of them) in place.  Arguments as for cta_build_tree; smem holds
 // smem_build_bytes(ns, sc, DC) bytes with sc = smem_seg_cap(ns, leaf).
+// root_slot >= 0: the root, if it splits, goes to that node slot (outside
+// node_base .. node_base + n - 2) instead of its split position.
 template <int DC, int NT>
 __device__ CtaTree cta_build_smem(float4 *P, int s0, int s1, const int *root_lo, const int *root_hi,
                                   unsigned char *smem, int ns, int sc, int leaf, int node_base, float4 *nodes,
                                   int *n_sdim, float *n_sval, int2 *n_range, int depth0 = 0,
-                                  int *n_parent = nullptr, int *leaf_parent = nullptr, int root_code = -1) {
+                                  int *n_parent = nullptr, int *leaf_parent = nullptr, int root_code = -1,
+                                  int root_slot = -1) {
     constexpr int W = bucket_w(DC);
     constexpr int NW = node_w(DC);
     constexpr uint16_t NONE = 0xffff;
@@ -218,7 +221,7 @@ __device__ CtaTree cta_build_smem(float4 *P, int s0, int s1, const int *root_lo,
             int node = -1, nl = 0;
             if (split) {
                 nl = ballot_prefix(m.word, m.wpre, en) - ballot_prefix(m.word, m.wpre, st);
-                node = node_base + st + nl - 1;
+                node = (level == 0 && root_slot >= 0) ? root_slot : node_base + st + nl - 1;
             }
             if (level == 0) {
                 s_root[0] = split ? node : s0 + st;

@@ -47,6 +47,43 @@ pg_status gather_points(const float *store, const int32_t *ids, int64_t n, int d
 // (it becomes the tree's bucket array or is freed).
 pg_status build_packed(float4 *packed, int64_t n, int dim, int leaf, cudaStream_t s, pg_tree *t);
 void tree_release(pg_tree *t);
+// Device-level splitting of many independent trees at once (build.cu).
+// Tree t starts as the segment [t_start[t], t_end[t]) of P with tight box
+// t_box[t*2*DC ...] (DC lows then DC highs, order-preserving ints); seg_of[i]
+// must hold the tree of position i (-1 for unused positions).  `levels`
+// levels are enqueued without host waits; segments of up to fin_max points,
+// and at the last level every segment that could still split, go to the
+// finisher list `fin` (start, end, parent, side, depth, lo, hi; fin_cap
+// entries per field; parent -(t+2) marks the root of tree t).  A finisher
+// segment [st, en) owns node slots [st, en) and must put its root in slot
+// en - 1, which its parent record (or roots[2t], roots[2t+1] for a tree root)
+// already names; level nodes get slots from node_off on.
+// The control block holds the node count, the finisher count and the number
+// of levels that moved points (its parity names the buffer that holds the
+// final order: P if even).
+struct ForestArgs {
+    int64_t n;
+    int ntrees, leaf, fin_max, levels, seg_cap, fin_cap, node_off;
+    float4 *P, *Q;
+    int *seg_of, *seg_of_nx;
+    const int *t_start, *t_end, *t_box;
+    float4 *nodes;
+    int *n_sdim;
+    float *n_sval;
+    int2 *n_range;
+    int *n_parent, *roots;
+    // carved from one scratch block by forest_carve
+    int *seg_a, *seg_b, *lvl, *fin, *ctl, *scan_ws;
+    unsigned *tiles;
+};
+struct ForestCtl {
+    int nb, fin, scatters;   // word indices in the control block
+};
+int64_t forest_words(int dc, int seg_cap, int fin_cap, int64_t n);
+void forest_carve(ForestArgs &fa, int *words, int dc);
+ForestCtl forest_ctl();
+pg_status forest_levels(int dc, const ForestArgs &fa, cudaStream_t s);
+
 pg_status tree_upload_desc(pg_tree *t);
 TreeDesc tree_desc(const pg_tree *t);
 
