@@ -183,7 +183,7 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
 // insertions then run converged (as many rounds as the busiest lane needs).
 // Each lane's pruning uses only its own k-th distance, so the answer is the
 // same exact k-NN as the other variants.
-template <int DC, int KC>
+template <int DC, int KC, bool NC = true>
 __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict__ bucket, int lref, int lcnt,
                                                         const float *q, KList<KC> &L) {
     const int maxc = __reduce_max_sync(0xffffffffu, lcnt);
@@ -195,7 +195,7 @@ __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict
             if (base + j < lcnt) {
                 float p[DC];
                 unsigned pid;
-                load_point<DC>(bucket, lref + base + j, p, pid);
+                load_point<DC, NC>(bucket, lref + base + j, p, pid);
                 const float dd = sqdist<DC>(q, p);
                 mask |= (pair_key(dd, pid) < kk ? 1u : 0u) << j;
             }
@@ -207,13 +207,13 @@ __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict
             mask &= mask - 1;
             float p[DC];
             unsigned pid;
-            load_point<DC>(bucket, act ? lref + base + j : lref, p, pid);
+            load_point<DC, NC>(bucket, act ? lref + base + j : lref, p, pid);
             L.offer_pred(sqdist<DC>(q, p), pid, act);
         }
     }
 }
 
-template <int DC, int KC>
+template <int DC, int KC, bool NC = true>
 __device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q, bool valid, KList<KC> &L) {
     constexpr int NW = node_w(DC);
     int s_ref[KNN_STACK], s_cnt[KNN_STACK];
@@ -251,7 +251,7 @@ __device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q
                     const float4 *np = T.nodes + (size_t)ref * NW;
 #pragma unroll
                     for (int w = 0; w < NW; ++w) {
-                        float4 f = __ldg(np + w);
+                        float4 f = ld4<NC>(np + w);
                         rec[4 * w] = f.x; rec[4 * w + 1] = f.y; rec[4 * w + 2] = f.z; rec[4 * w + 3] = f.w;
                     }
                     const int *ri = reinterpret_cast<const int *>(rec + 4 * DC);
@@ -276,7 +276,7 @@ __device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q
         }
         if (!__any_sync(0xffffffffu, lcnt > 0)) break;
         // leaf phase, converged
-        scan_own_leaf_converged<DC, KC>(T.bucket, lref, lcnt, q, L);
+        scan_own_leaf_converged<DC, KC, NC>(T.bucket, lref, lcnt, q, L);
         lcnt = 0;
     }
 }
