@@ -128,14 +128,18 @@ def kernel_sha(names):
 KNN_SOURCES = ["knn_kernel.cuh", "common.cuh", "knn_dc3.cu"]
 
 
-def traffic_for(kernel: str, sha: str, units: int):
-    """ncu DRAM bytes per launch from profiles/, if taken on this kernel source."""
+KNN_KERNELS = {1: "k_knn", 2: "k_knn_packet", 3: "k_knn_ww"}
+
+
+def traffic_for(kernel: str, sha: str, units: int, variant: int, leaf: int):
+    """ncu DRAM bytes per launch from profiles/, if taken on this kernel source
+    with the same traversal variant and leaf size."""
     path = os.path.join(ROOT, "profiles", f"{kernel}.traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    if d.get("source_sha") != sha:
+    if d.get("source_sha") != sha or d.get("variant") != variant or d.get("leaf") != leaf:
         return None
     return float(d["dram_bytes_per_unit"]) * units
 
@@ -474,9 +478,10 @@ def run_ours(args):
     knn_avg_ms = knn_ms / max(knn_launches, 1)
     achieved = alg_bytes / (knn_avg_ms / 1e3) / 1e9
     sha = kernel_sha(KNN_SOURCES)
-    roofline = {"bound": "hbm", "kernel": "k_knn<3,10> (knn_traverse)", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": f"{KNN_KERNELS.get(variant, 'k_knn')}<3,10> (knn_traverse)",
+                "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_for("knn_traverse", sha, n), "alg_bytes_per_launch": alg_bytes,
+                "traffic": traffic_for("knn_traverse", sha, n, variant, leaf), "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": knn_avg_ms, "launches_timed": knn_launches, "source_sha": sha}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
