@@ -19,7 +19,7 @@ from . import api
 from .build import OUT_DIR
 
 CACHE = os.path.join(OUT_DIR, "autotune.json")
-LEAF_CANDIDATES = (8, 16, 32)
+LEAF_CANDIDATES = (8, 16, 32, 48, 64)
 VARIANT_CANDIDATES = (1, 2, 3)   # thread per query, warp packets, postponed leaves
 _lock = threading.Lock()
 

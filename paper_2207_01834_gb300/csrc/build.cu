@@ -116,23 +116,23 @@ __device__ __forceinline__ unsigned seg_combine(unsigned a, unsigned b) {   // a
 // Flags and segment starts of one tile; every warp-row's segmented count
 // goes to rowsum[row * PT_WARPS + warp].
 template <int DC>
-__device__ __forceinline__ void tile_flags(int64_t n, int64_t base, const float *pf, const int *seg_of,
+__device__ __forceinline__ void tile_flags(int n, int base, const float *pf, const int *seg_of,
                                            const int *split_flag, const int *sdim, const float *sval,
-                                           unsigned &fbits, unsigned &rbits, int *srow, unsigned *rowsum) {
+                                           unsigned &fbits, unsigned &rbits, unsigned *rowsum) {
     constexpr int W = bucket_w(DC);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     fbits = 0;
     rbits = 0;
 #pragma unroll
     for (int j = 0; j < PT_ROWS; ++j) {
-        const int64_t i = base + j * PT_THREADS + threadIdx.x;
+        const int i = base + j * PT_THREADS + threadIdx.x;
         const bool valid = i < n;
         const int s = valid ? seg_of[i] : -1;
-        const int sp = (valid && i > 0) ? seg_of[i - 1] : -2;
+        int sp = __shfl_up_sync(0xffffffffu, s, 1);   // position i - 1 (same warp row)
+        if (lane == 0) sp = (valid && i > 0) ? seg_of[i - 1] : -2;
         const bool start = valid && s != sp;
         int f = 0;
-        if (valid && s >= 0 && split_flag[s]) f = pf[i * 4 * W + sdim[s]] < sval[s];
-        srow[j] = s;
+        if (valid && s >= 0 && split_flag[s]) f = pf[(size_t)i * 4 * W + sdim[s]] < sval[s];
         fbits |= (unsigned)f << j;
         rbits |= (unsigned)start << j;
         const unsigned F = __ballot_sync(0xffffffffu, f), R = __ballot_sync(0xffffffffu, start);
@@ -153,9 +153,8 @@ __global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const floa
     if (*T == 0) return;
     __shared__ unsigned rowsum[PT_ROWS * PT_WARPS];
     unsigned fbits, rbits;
-    int srow[PT_ROWS];
-    tile_flags<DC>(n, (int64_t)blockIdx.x * PT_TILE, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim,
-                   sval, fbits, rbits, srow, rowsum);
+    tile_flags<DC>((int)n, blockIdx.x * PT_TILE, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval,
+                   fbits, rbits, rowsum);
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned a = 0;
@@ -352,7 +351,7 @@ __global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__rest
 // of a tile are few and consecutive), then one global atomic per child and
 // dimension; a child that finds its slot taken goes straight to global memory.
 template <int DC>
-__global__ void __launch_bounds__(PT_THREADS) k_part(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
+__global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
                                                      const int *__restrict__ seg_of, int *__restrict__ seg_of_nx,
                                                      const int *__restrict__ start, const int *__restrict__ end,
                                                      const int *__restrict__ split_flag,
@@ -367,15 +366,15 @@ __global__ void __launch_bounds__(PT_THREADS) k_part(int64_t n, const float4 *__
     __shared__ int tag[kBoxSlots];
     __shared__ int b_lo[kBoxSlots * DC], b_hi[kBoxSlots * DC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * PT_TILE;
+    const int base = blockIdx.x * PT_TILE;
+    const int n32 = (int)n;
     if (threadIdx.x < kBoxSlots) tag[threadIdx.x] = -1;
     for (int x = threadIdx.x; x < kBoxSlots * DC; x += PT_THREADS) {
         b_lo[x] = 0x7f800000;
         b_hi[x] = (int)0x807fffffu;
     }
     unsigned fbits, rbits;
-    int srow[PT_ROWS];
-    tile_flags<DC>(n, base, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval, fbits, rbits, srow,
+    tile_flags<DC>(n32, base, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval, fbits, rbits,
                    rowsum);
     __syncthreads();
     // segmented exclusive scan of the tile's warp-rows (warp 0, 4 per lane)
@@ -404,8 +403,12 @@ __global__ void __launch_bounds__(PT_THREADS) k_part(int64_t n, const float4 *__
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < PT_ROWS; ++j) {
-        const int64_t i = base + j * PT_THREADS + threadIdx.x;
-        const bool valid = i < n;
+        const int i = base + j * PT_THREADS + threadIdx.x;
+        const bool valid = i < n32;
+        float4 v[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) v[w] = valid ? P[(size_t)i * W + w] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int s = valid ? seg_of[i] : -1;
         const int f = (fbits >> j) & 1u;
         const unsigned F = __ballot_sync(0xffffffffu, f);
         const unsigned R = __ballot_sync(0xffffffffu, (rbits >> j) & 1u);
@@ -413,19 +416,13 @@ __global__ void __launch_bounds__(PT_THREADS) k_part(int64_t n, const float4 *__
         int r;
         if (m) r = __popc(F & lt & ~((1u << (31 - __clz(m))) - 1u));
         else r = (int)(rowsum[j * PT_WARPS + warp] & 0x7fffffffu) + __popc(F & lt);
-        const int s = srow[j];
         int child = -1;
-        float4 v[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) v[w] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) v[w] = P[i * W + w];
-            int64_t dst = i;
+            int dst = i;
             if (s >= 0 && split_flag[s]) {
                 const int st = start[s], en = end[s], rk = split_rank[s];
                 if (f) { dst = st + r; child = 2 * rk; }
-                else { dst = en - 1 - ((int)(i - st) - r); child = 2 * rk + 1; }
+                else { dst = en - 1 - ((i - st) - r); child = 2 * rk + 1; }
                 if (i == en - 1) {
                     const int nl = r + f;
                     nx_start[2 * rk] = st;
@@ -435,7 +432,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_part(int64_t n, const float4 *__
                 }
             }
 #pragma unroll
-            for (int w = 0; w < W; ++w) Q[dst * W + w] = v[w];
+            for (int w = 0; w < W; ++w) Q[(size_t)dst * W + w] = v[w];
             seg_of_nx[dst] = child;
         }
         const float *cf = reinterpret_cast<const float *>(v);
