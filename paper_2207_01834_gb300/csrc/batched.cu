@@ -461,8 +461,7 @@ extern "C" pg_status pg_batched_chamfer(const float *a, const int64_t *a_off, co
     for (int i = 0; i < pl->graph_kernels; ++i) count_launch();   // the graph's kernel nodes
     PG_CUDA(cudaMemcpyAsync(loss, pl->loss_dev, sizeof(float) * npairs, cudaMemcpyDeviceToDevice, s));
     int st = 0;
-    PG_CUDA(cudaMemcpyAsync(&st, pl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PG_CUDA(cudaStreamSynchronize(s));
+    PG_TRY(read_small(&st, pl->status, sizeof(int), s));
     if (st == 1) return fail(PG_ETIMEOUT, "pg_batched_chamfer: a query waited too long for a tree");
     // st == 2: a finisher ran out of scratch and kept one leaf (results stay exact)
     return PG_OK;

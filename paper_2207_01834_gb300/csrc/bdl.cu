@@ -190,8 +190,7 @@ pg_status bdl_collect(pg_bdl *b, uint64_t mask, bool want_buf, Scratch &out, int
     }
     PG_TRY(exclusive_scan(flags.as<int>(), pre.as<int>(), n, b->s));
     int h = 0;
-    PG_CUDA(cudaMemcpyAsync(&h, pre.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, b->s));
-    PG_CUDA(cudaStreamSynchronize(b->s));
+    PG_TRY(read_small(&h, pre.as<int>() + n, sizeof(int), b->s));
     PG_TRY(out.alloc(sizeof(int32_t) * (size_t)std::max(h, 1), b->s));
     if (h > 0) {
         k_compact<<<grid_of(n), BT, 0, b->s>>>(flags.as<int>(), pre.as<int>(), n, out.as<int32_t>());
@@ -366,8 +365,7 @@ pg_status erase_impl(pg_bdl *b, const float *pts, int64_t cnt) {
         PG_TRY(st);
     }
     std::vector<int> erased(trees.size());
-    PG_CUDA(cudaMemcpyAsync(erased.data(), cnts.p, sizeof(int) * trees.size(), cudaMemcpyDeviceToHost, b->s));
-    PG_CUDA(cudaStreamSynchronize(b->s));
+    PG_TRY(read_small(erased.data(), cnts.p, sizeof(int) * trees.size(), b->s));
     uint64_t destroy = 0;
     for (size_t t = 0; t < trees.size(); ++t) {
         if (erased[t] == 0) continue;

@@ -679,8 +679,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         std::swap(seg_of, seg_of_nx);
         std::swap(cur, nxt);
         if (level + 1 >= est) {
-            PG_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(hctl), cudaMemcpyDeviceToHost, s));
-            PG_CUDA(cudaStreamSynchronize(s));
+            PG_TRY(read_small(hctl, ctl, sizeof(hctl), s));
             if (hctl[CTL_DONE]) break;
         }
     }
@@ -708,8 +707,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
         }
         PG_TRY(check_launch("build finish"));
         int h[3];
-        PG_CUDA(cudaMemcpyAsync(h, rec, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
-        PG_CUDA(cudaStreamSynchronize(s));
+        PG_TRY(read_small(h, rec, sizeof(int) * 3, s));
         t->depth = std::max(t->depth, h[2]);
         if (!root_split) {   // the whole tree was one finisher segment
             t->root_ref = h[0];
@@ -911,8 +909,7 @@ static pg_status build_from(const float *src, const int32_t *rows, const int32_t
     PG_DC_SWITCH(dc, st = pack_impl<DCV>(src, rows, ids, n, dim, packed, box.as<int>(), s));
     if (st != PG_OK) { dfree(packed, s); return st; }
     int hbox[2 * PG_MAX_DIM];
-    PG_CUDA(cudaMemcpyAsync(hbox, box.as<int>(), sizeof(int) * 2 * dc, cudaMemcpyDeviceToHost, s));
-    PG_CUDA(cudaStreamSynchronize(s));
+    PG_TRY(read_small(hbox, box.as<int>(), sizeof(int) * 2 * dc, s));
     for (int c = 0; c < PG_MAX_DIM; ++c) { t->root_lo[c] = 0.f; t->root_hi[c] = 0.f; }
     for (int c = 0; c < dc; ++c) {
         int a = hbox[c], b = hbox[dc + c];

@@ -75,6 +75,9 @@ struct KTimer {
     ~KTimer();
 };
 pg_status check_launch(const char *what);
+// Copy up to 1024 bytes (whole words) of device memory to the host, in stream
+// order, without a copy engine; synchronises the stream.
+pg_status read_small(void *host_dst, const void *dev_src, size_t bytes, cudaStream_t s);
 
 inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 int num_sms();

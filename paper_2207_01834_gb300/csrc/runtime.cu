@@ -2,6 +2,7 @@
 // counting and the kernel timer used for roofline measurements.
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -64,6 +65,35 @@ void dfree(void *p, cudaStream_t s) {
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// ---------------------------------------------------------------- small reads
+// A few device words reach the host through a kernel that stores them into
+// mapped pinned host memory, not through a copy engine: a bulk transfer the
+// caller has in flight on another stream (results going back to the host)
+// then cannot delay the library's own control reads.
+namespace {
+__global__ void k_read_small(const int *__restrict__ src, int *dst, int words) {
+    const int i = threadIdx.x;
+    if (i < words) dst[i] = src[i];
+}
+constexpr size_t kReadSmallBytes = 1024;
+thread_local std::map<int, int *> t_mapped;   // device -> mapped buffer (kept for the thread's life)
+}  // namespace
+
+pg_status read_small(void *host_dst, const void *dev_src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return PG_OK;
+    if (bytes > kReadSmallBytes || bytes % 4) return fail(PG_EINVAL, "read_small: at most 1024 bytes, whole words");
+    int dev = 0;
+    PG_CUDA(cudaGetDevice(&dev));
+    int *&buf = t_mapped[dev];
+    if (!buf) PG_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&buf), kReadSmallBytes, cudaHostAllocMapped | cudaHostAllocPortable));
+    k_read_small<<<1, (int)(kReadSmallBytes / 4), 0, s>>>(static_cast<const int *>(dev_src), buf, (int)(bytes / 4));
+    count_launch();
+    PG_TRY(check_launch("read_small"));
+    PG_CUDA(cudaStreamSynchronize(s));
+    memcpy(host_dst, buf, bytes);
+    return PG_OK;
+}
+
 
 pg_status check_launch(const char *what) {
     cudaError_t e = cudaGetLastError();
