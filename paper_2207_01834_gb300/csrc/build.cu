@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n,
     }
 }
 
-constexpr int FIN_NT = 256;                  // threads of a finisher block
+constexpr int FIN_NT = 512;                  // threads of a finisher block
 constexpr size_t kFinSmemBudget = 110 * 1024;   // shared memory of a finisher block (two blocks per SM)
 
 // Segments small enough for one block's shared memory are finished by the
