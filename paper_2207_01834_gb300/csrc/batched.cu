@@ -71,17 +71,21 @@ __global__ void k_bbounds(const uint32_t *__restrict__ sk, int64_t P, uint32_t n
 // Gradient of sum_i g_i loss_i for the rows of one array X (the other array
 // is Y):  direct part from X's own k neighbours in Y, then the contributions
 // of every Y row that selected this X row, in ascending (row, slot) order.
-// Rows selected more than kHeavy times are finished by k_bgrad_heavy (one
-// warp per row) so that a few hub points do not hold whole warps back.
+// A row selected more than kHeavy times (a hub) is split into chunks of
+// kChunk entries: one warp sums a chunk (lane l takes entries l, l+32, ... in
+// order, then a fixed butterfly), and the row adds its chunk sums in chunk
+// order.  Every order is fixed, so the result is the same on every run, and
+// no warp is held back by one hub.
 constexpr int kHeavy = 64;
+constexpr int kChunk = 256;
 
 template <int DC>
 __global__ void k_bgrad(const float *__restrict__ X, int64_t nx, const float *__restrict__ Y, int dim, int k,
                         const int32_t *__restrict__ idx_xy, const int *__restrict__ row_pair_x,
                         const int *__restrict__ row_pair_y, const long long *__restrict__ off_y,
                         const float *__restrict__ g, const uint32_t *__restrict__ sv_yx, const int *__restrict__ lo,
-                        const int *__restrict__ hi, float *__restrict__ gx, int *__restrict__ heavy,
-                        int *__restrict__ nheavy) {
+                        const int *__restrict__ hi, float *__restrict__ gx, int2 *__restrict__ heavy,
+                        int *__restrict__ nheavy, int *__restrict__ chunk_row, int *__restrict__ nchunks) {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nx) return;
     float p[DC], acc[DC];
@@ -103,7 +107,12 @@ __global__ void k_bgrad(const float *__restrict__ X, int64_t nx, const float *__
     }
     const int e0 = lo[x], e1 = hi[x];
     if (e1 - e0 > kHeavy) {
-        heavy[atomicAdd(nheavy, 1)] = (int)x;     // list order does not affect any sum
+        // list positions and chunk slots do not affect any sum
+        const int nch = (e1 - e0 + kChunk - 1) / kChunk;
+        const int first = atomicAdd(nchunks, nch);
+        const int h = atomicAdd(nheavy, 1);
+        heavy[h] = make_int2((int)x, first);
+        for (int c = 0; c < nch; ++c) chunk_row[first + c] = h;
     } else {
         for (int e = e0; e < e1; ++e) {
             const uint32_t v = sv_yx[e];
@@ -119,28 +128,29 @@ __global__ void k_bgrad(const float *__restrict__ X, int64_t nx, const float *__
         if (c < dim) gx[x * dim + c] = acc[c];
 }
 
-// One warp per heavy row: lane l sums entries l, l+32, ... in order, then a
-// fixed butterfly adds the lanes; the row's direct part (already in gx) is
-// added last.  The order is the same on every run.
+// One warp per chunk of a hub row: the chunk's sum goes to part[slot].
 template <int DC>
-__global__ void k_bgrad_heavy(const float *__restrict__ X, const float *__restrict__ Y, int dim, int k,
+__global__ void k_bgrad_chunk(const float *__restrict__ X, const float *__restrict__ Y, int dim, int k,
                               const int *__restrict__ row_pair_y, const float *__restrict__ g,
                               const uint32_t *__restrict__ sv_yx, const int *__restrict__ lo,
-                              const int *__restrict__ hi, float *__restrict__ gx, const int *__restrict__ heavy,
-                              const int *__restrict__ nheavy) {
+                              const int *__restrict__ hi, const int2 *__restrict__ heavy,
+                              const int *__restrict__ chunk_row, const int *__restrict__ nchunks,
+                              float *__restrict__ part) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int cnt = *nheavy;
-    for (int64_t h = wid; h < cnt; h += nw) {
-        const int64_t x = heavy[h];
+    const int cnt = *nchunks;
+    for (int64_t slot = wid; slot < cnt; slot += nw) {
+        const int2 hr = heavy[chunk_row[slot]];
+        const int64_t x = hr.x;
+        const int e0 = lo[x] + (int)(slot - hr.y) * kChunk, e1 = min(hi[x], e0 + kChunk);
         float p[DC], acc[DC];
 #pragma unroll
         for (int c = 0; c < DC; ++c) {
             p[c] = c < dim ? X[x * dim + c] : 0.f;
             acc[c] = 0.f;
         }
-        for (int e = lo[x] + lane; e < hi[x]; e += 32) {
+        for (int e = e0 + lane; e < e1; e += 32) {
             const uint32_t v = sv_yx[e];
             const int64_t yr = v / (uint32_t)k;
             const float wy = -2.f * g[row_pair_y[yr]];
@@ -155,10 +165,31 @@ __global__ void k_bgrad_heavy(const float *__restrict__ X, const float *__restri
         }
         if (lane == 0) {
 #pragma unroll
-            for (int c = 0; c < DC; ++c)
-                if (c < dim) gx[x * dim + c] = __fadd_rn(gx[x * dim + c], acc[c]);
+            for (int c = 0; c < DC; ++c) part[slot * DC + c] = acc[c];
         }
     }
+}
+
+// One thread per hub row: direct part (already in gx) + chunk sums in order.
+template <int DC>
+__global__ void k_bgrad_hubs(int dim, const int *__restrict__ lo, const int *__restrict__ hi,
+                             const int2 *__restrict__ heavy, const int *__restrict__ nheavy,
+                             const float *__restrict__ part, float *__restrict__ gx) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= *nheavy) return;
+    const int2 hr = heavy[h];
+    const int64_t x = hr.x;
+    const int nch = (hi[x] - lo[x] + kChunk - 1) / kChunk;
+    float acc[DC];
+#pragma unroll
+    for (int c = 0; c < DC; ++c) acc[c] = 0.f;
+    for (int j = 0; j < nch; ++j) {
+#pragma unroll
+        for (int c = 0; c < DC; ++c) acc[c] = __fadd_rn(acc[c], part[(int64_t)(hr.y + j) * DC + c]);
+    }
+#pragma unroll
+    for (int c = 0; c < DC; ++c)
+        if (c < dim) gx[x * dim + c] = __fadd_rn(gx[x * dim + c], acc[c]);
 }
 
 inline int grid_of(int64_t n) { return std::max(1, ceil_div_i(n, BT)); }
@@ -501,10 +532,17 @@ extern "C" pg_status pg_batched_chamfer_backward(const float *a, const int64_t *
     count_launch();
     const int64_t Pab = Na * k, Pba = Nb * k, Pm = std::max(Pab, Pba);
     // keys, vals, two temporaries (for the larger direction) + bounds for a and b
-    PG_TRY(sc.alloc(sizeof(uint32_t) * (size_t)(4 * Pm) + sizeof(int) * (size_t)(3 * std::max(Na, Nb) + 1) + 256, s));
+    // hub rows hold more than kHeavy entries each: at most Pm/kHeavy of them,
+    // and at most Pm/kChunk + Pm/kHeavy chunks
+    const int64_t Nm = std::max(Na, Nb), Hm = Pm / kHeavy + 1, Cm = Pm / kChunk + Hm;
+    PG_TRY(sc.alloc(sizeof(uint32_t) * (size_t)(4 * Pm) + sizeof(int) * (size_t)(2 * Nm + 2 * Hm + Cm + 2) +
+                        sizeof(float) * (size_t)(Cm * dim_class(dim)) + 256, s));
     uint32_t *keys = sc.as<uint32_t>(), *vals = keys + Pm, *tk = vals + Pm, *tv = tk + Pm;
-    int *lo = reinterpret_cast<int *>(tv + Pm), *hi = lo + std::max(Na, Nb);
-    int *heavy = hi + std::max(Na, Nb), *nheavy = heavy + std::max(Na, Nb);
+    int *lo = reinterpret_cast<int *>(tv + Pm), *hi = lo + Nm;
+    int2 *heavy = reinterpret_cast<int2 *>(hi + Nm);
+    int *chunk_row = reinterpret_cast<int *>(heavy + Hm);
+    int *nheavy = chunk_row + Cm, *nchunks = nheavy + 1;
+    float *part = reinterpret_cast<float *>(nchunks + 1);
     auto bits_for = [](int64_t n) { int b = 1; while (b < 32 && ((int64_t)1 << b) <= n) ++b; return b; };
     // grad_b: b rows' own neighbours in a (idx_ba) + a rows that selected them (idx_ab)
     for (int side = 0; side < 2; ++side) {
@@ -514,29 +552,30 @@ extern "C" pg_status pg_batched_chamfer_backward(const float *a, const int64_t *
         const int *rpy = for_b ? rpa : rpb;
         const long long *offx = for_b ? boff : aoff;
         const int64_t P = ny * k;
-        PG_CUDA(cudaMemsetAsync(lo, 0, sizeof(int) * (size_t)(2 * std::max(Na, Nb)), s));
+        PG_CUDA(cudaMemsetAsync(lo, 0, sizeof(int) * (size_t)(2 * Nm), s));
         k_bkeys<<<grid_of(P), BT, 0, s>>>(idx_yx, ny, k, rpy, offx, (uint32_t)nx, keys);
         count_launch();
         uint32_t *sk, *sv;
         PG_TRY(radix_sort_pairs(keys, vals, true, tk, tv, P, bits_for(nx), s, &sk, &sv));
-        k_bbounds<<<grid_of(P), BT, 0, s>>>(sk, P, (uint32_t)nx, lo, lo + std::max(Na, Nb));
+        k_bbounds<<<grid_of(P), BT, 0, s>>>(sk, P, (uint32_t)nx, lo, hi);
         count_launch();
         KTimer kt("batched_backward_grad", s);
-        PG_CUDA(cudaMemsetAsync(nheavy, 0, sizeof(int), s));
+        PG_CUDA(cudaMemsetAsync(nheavy, 0, sizeof(int) * 2, s));
         const float *Xp = for_b ? b : a, *Yp = for_b ? a : b;
         const int32_t *ixy = for_b ? idx_ba : idx_ab;
         const int *rpx = for_b ? rpb : rpa;
         const long long *offy = for_b ? aoff : boff;
         float *gxp = for_b ? grad_b : grad_a;
-        int *hi_arr = lo + std::max(Na, Nb);
+        int *hi_arr = hi;
         const int hgrid = num_sms() * 8;
         switch (dim_class(dim)) {
 #define PG_BG(D)                                                                                            \
             case D:                                                                                         \
                 k_bgrad<D><<<grid_of(nx), BT, 0, s>>>(Xp, nx, Yp, dim, k, ixy, rpx, rpy, offy, grad_loss, sv, lo, \
-                                                      hi_arr, gxp, heavy, nheavy);                          \
-                k_bgrad_heavy<D><<<hgrid, BT, 0, s>>>(Xp, Yp, dim, k, rpy, grad_loss, sv, lo, hi_arr, gxp,  \
-                                                      heavy, nheavy);                                       \
+                                                      hi_arr, gxp, heavy, nheavy, chunk_row, nchunks);      \
+                k_bgrad_chunk<D><<<hgrid, BT, 0, s>>>(Xp, Yp, dim, k, rpy, grad_loss, sv, lo, hi_arr, heavy, \
+                                                      chunk_row, nchunks, part);                            \
+                k_bgrad_hubs<D><<<grid_of(Hm), BT, 0, s>>>(dim, lo, hi_arr, heavy, nheavy, part, gxp);      \
                 break;
             PG_BG(2) PG_BG(3) PG_BG(4) PG_BG(5) PG_BG(6) PG_BG(7) PG_BG(8) PG_BG(12) PG_BG(16)
 #undef PG_BG
@@ -544,8 +583,8 @@ extern "C" pg_status pg_batched_chamfer_backward(const float *a, const int64_t *
         }
         count_launch();
         count_launch();
+        count_launch();
         PG_TRY(check_launch("batched backward"));
     }
-    (void)hi;
     return PG_OK;
 }
