@@ -102,19 +102,19 @@ __device__ __forceinline__ void load_point(const float4 *__restrict__ bucket, in
     pid = __float_as_uint(v[DC]);
 }
 
-template <int DC, int KC>
+template <int DC, int KC, bool NC = true>
 __device__ __forceinline__ void scan_leaf(const float4 *__restrict__ bucket, int ref, int cnt, const float *q,
                                           KList<KC> &L) {
     for (int i = ref; i < ref + cnt; ++i) {
         float p[DC];
         unsigned pid;
-        load_point<DC>(bucket, i, p, pid);
+        load_point<DC, NC>(bucket, i, p, pid);
         const float d = sqdist<DC>(q, p);
         if (d <= L.kth()) L.offer(d, pid);   // cheap float test rejects most candidates
     }
 }
 
-template <int DC, int KC>
+template <int DC, int KC, bool NC = true>
 __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, KList<KC> &L) {
     if (T.root_cnt < 0) return;
     float rlo[DC], rhi[DC];
@@ -123,7 +123,7 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
     const float d_root = boxdist<DC>(q, rlo, rhi);
     if (d_root > L.kth()) return;
     if (T.root_cnt > 0) {
-        scan_leaf<DC, KC>(T.bucket, T.root_ref, T.root_cnt, q, L);
+        scan_leaf<DC, KC, NC>(T.bucket, T.root_ref, T.root_cnt, q, L);
         return;
     }
     int s_ref[KNN_STACK], s_cnt[KNN_STACK];
@@ -137,7 +137,7 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
         int cnt = s_cnt[sp];
         if (s_d[sp] > L.kth()) continue;
         if (cnt > 0) {
-            scan_leaf<DC, KC>(T.bucket, ref, cnt, q, L);
+            scan_leaf<DC, KC, NC>(T.bucket, ref, cnt, q, L);
             continue;
         }
         for (;;) {
@@ -145,7 +145,7 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
             const float4 *np = T.nodes + (size_t)ref * NW;
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
-                float4 f = __ldg(np + w);
+                float4 f = ld4<NC>(np + w);
                 rec[4 * w] = f.x; rec[4 * w + 1] = f.y; rec[4 * w + 2] = f.z; rec[4 * w + 3] = f.w;
             }
             const int *ri = reinterpret_cast<const int *>(rec + 4 * DC);
@@ -162,7 +162,7 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
             }
             if (cn >= 0 && dn <= kth) {
                 if (cn > 0) {
-                    scan_leaf<DC, KC>(T.bucket, rn, cn, q, L);
+                    scan_leaf<DC, KC, NC>(T.bucket, rn, cn, q, L);
                     break;
                 }
                 ref = rn;
