@@ -194,7 +194,7 @@ __global__ void k_bgrad_hubs(int dim, const int *__restrict__ lo, const int *__r
 
 inline int grid_of(int64_t n) { return std::max(1, ceil_div_i(n, BT)); }
 
-constexpr size_t kBatchSmemBudget = 110 * 1024;   // finisher shared memory per block (two blocks per SM)
+constexpr size_t kBatchSmemBudget = 52 * 1024;    // finisher shared memory per block (leaves room for query occupancy)
 
 __global__ void k_bpending(BDev D) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;

@@ -154,7 +154,7 @@ __global__ void k_bbox_init(int *cl_box, int ncl) {
 }
 
 template <int DC, int KC>
-__global__ void __launch_bounds__(BATCH_NT) k_batched(const BArgs *__restrict__ args, BDev D) {
+__global__ void __launch_bounds__(BATCH_NT, KC <= 16 ? 4 : 2) k_batched(const BArgs *__restrict__ args, BDev D) {
     constexpr int NT = BATCH_NT;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
