@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-extras", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--batched-only", type=int, default=0, metavar="K",
+                   help="time only the batched Chamfer forward + backward with this k (for profiling)")
     return p.parse_args()
 
 
@@ -220,6 +222,42 @@ def batched_vs_plain(api, torch, dev, k: int, reps: int = 3):
     return {"workload": "256 pairs of 3D clouds, sizes log-uniform [1e3, 1e5], 8-component GMM each",
             "points": int(a_off[-1] + b_off[-1]), "k": k, "batched_fwd_bwd_ms": tb_ms,
             "plain_fwd_bwd_ms": tp_ms, "speedup": tp_ms / tb_ms, "identical_indices": same}
+
+
+def batched_only(args):
+    """Only the batched Chamfer forward + backward on the 256-pair workload:
+    `warmup` untimed passes, then `steps` timed ones (CUDA events)."""
+    import torch
+
+    from paper_2207_01834_gb300 import api, synth
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    k = args.batched_only
+    a, a_off, b, b_off = synth.cloud_pairs(256, seed=synth.BASE_SEED + 5)
+    A = torch.from_numpy(a).to(dev)
+    B = torch.from_numpy(b).to(dev)
+    g = torch.ones(256, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        _, iab, iba, _, _ = api.pg_batched_chamfer(A, a_off, B, b_off, k)
+        api.pg_batched_chamfer_backward(A, a_off, B, b_off, k, iab, iba, g)
+    torch.cuda.synchronize()
+    fwd, bwd = [], []
+    for _ in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        _, iab, iba, _, _ = api.pg_batched_chamfer(A, a_off, B, b_off, k)
+        e[1].record(stream)
+        api.pg_batched_chamfer_backward(A, a_off, B, b_off, k, iab, iba, g)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fwd.append(e[0].elapsed_time(e[1]))
+        bwd.append(e[1].elapsed_time(e[2]))
+    print(json.dumps({"metric": "batched Chamfer forward + backward", "unit": "ms", "k": k,
+                      "workload": "256 pairs of 3D clouds, sizes log-uniform [1e3, 1e5], 8-component GMM each",
+                      "points": int(a_off[-1] + b_off[-1]), "steps": args.steps, "warmup": args.warmup,
+                      "fwd_ms": statistics.median(fwd), "bwd_ms": statistics.median(bwd)}), flush=True)
 
 
 def other_configs(api, torch, dev):
@@ -552,6 +590,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.batched_only > 0:
+        batched_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
