@@ -1,7 +1,7 @@
-"""GPU batched multi-cloud path (one persistent launch for every cloud's build
-and every query chunk) against the per-cloud plain path (bit for bit) and the
-CPU oracle; its backward twin against the oracle's gradient and float64
-finite differences."""
+"""GPU batched multi-cloud path (the level kernels split every cloud's tree at
+once, then one persistent launch finishes the segments and runs every query
+chunk) against the per-cloud plain path (bit for bit) and the CPU oracle; its
+backward twin against the oracle's gradient and float64 finite differences."""
 from __future__ import annotations
 
 import numpy as np
@@ -73,6 +73,31 @@ def test_batched_matches_plain_and_oracle(api, dim, k, seed):
     # replaying the cached plan gives the same bits
     loss2, iab2, iba2, _, _ = api.pg_batched_chamfer(_cuda(a), a_off, _cuda(b), b_off, k)
     assert torch.equal(loss, loss2) and torch.equal(iab, iab2) and torch.equal(iba, iba2)
+
+
+def test_batched_deep_cloud_takes_the_global_memory_finisher(api):
+    """A dense cluster behind a geometric row of outliers: every spatial-median
+    level peels off about one outlier, so after all the forest levels the
+    cluster is still one segment far above the shared-memory capacity and is
+    finished by the global-memory block builder (scratch from the pool)."""
+    rng = np.random.default_rng(31)
+    cluster = (0.3 + 1e-5 * rng.random((12000, 3))).astype(np.float32)
+    row = np.zeros((40, 3), np.float32)
+    row[:, 0] = (0.3 + 2.0 ** -np.arange(40)).astype(np.float32)
+    row[:, 1:] = 0.3
+    deep = np.concatenate([cluster, row])[rng.permutation(12040)]
+    other = synth.cloud(3000, 3, 32)
+    a = np.concatenate([deep, other]).astype(np.float32)
+    b = np.concatenate([synth.cloud(2000, 3, 33), deep[::3]]).astype(np.float32)
+    a_off = np.array([0, 12040, 15040])
+    b_off = np.array([0, 2000, 2000 + len(deep[::3])])
+    k = 8
+    loss, iab, iba, dab, dba = api.pg_batched_chamfer(_cuda(a), a_off, _cuda(b), b_off, k, want_dist=True)
+    p_iab, p_dab, p_iba, p_dba = _plain(api, a, a_off, b, b_off, k)
+    assert torch.equal(iab, p_iab) and torch.equal(dab, p_dab)
+    assert torch.equal(iba, p_iba) and torch.equal(dba, p_dba)
+    _check_against_oracle(a, a_off, b, b_off, k, iab.cpu().numpy(), dab.cpu().numpy(), iba.cpu().numpy(),
+                          dba.cpu().numpy(), loss.cpu().numpy(), rows_per_pair=600)
 
 
 def test_batched_tiny_clouds_and_padding(api):
