@@ -295,21 +295,25 @@ def other_configs(api, torch, dev):
     qms = timed(q2)
     out["2d_20k_k5"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 20000 / qms / 1e3}
     # 5D / 7D clustered: 2,000,000 points, 1,000,000 separate queries, k = 16
+    # (leaf size and traversal variant autotuned on the workload itself)
+    from paper_2207_01834_gb300 import autotune
     for d in (5, 7):
         mix = synth.gmm_mixture(d, synth.BASE_SEED + 3)
         pts = torch.from_numpy(synth.gmm_sample(2_000_000, mix, synth.BASE_SEED + 30 + d)).to(dev)
         q = torch.from_numpy(synth.gmm_sample(1_000_000, mix, synth.BASE_SEED + 40 + d)).to(dev)
+        leaf_d, var_d = autotune.best_config(pts, 16, queries=q)
         h = {}
 
         def bd():
-            h["t"] = api.pg_tree_build(pts, 16)
+            h["t"] = api.pg_tree_build(pts, leaf_d)
 
         def qd():
             api.pg_knn(h["t"], q, 16)
 
         bms = timed(bd)
         qms = timed(qd)
-        out[f"{d}d_gmm_2m_1mq_k16"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 1e6 / qms / 1e3}
+        out[f"{d}d_gmm_2m_1mq_k16"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 1e6 / qms / 1e3,
+                                       "leaf_size": leaf_d, "traversal_variant": var_d}
         h["t"].free()
     # batch-dynamic BDL schedule (3D uniform, buffer 65,536, k = 10 queries after every batch)
     f = api.BDL(3, 65536, 16)

@@ -164,7 +164,19 @@ __global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const floa
 }
 
 // Segmented exclusive scan over the tiles (one block).
-__global__ void __launch_bounds__(1024) k_part_carry(unsigned *__restrict__ tsum, int ntiles, const int *__restrict__ T) {
+__global__ void __launch_bounds__(1024) k_part_carry(unsigned *__restrict__ tsum, int ntiles, const int *__restrict__ T,
+                                                     int *__restrict__ ctl, const int *__restrict__ fin_total, int level) {
+    // end of the level: advance the control block (nothing after this kernel
+    // in the level reads it)
+    if (threadIdx.x == 0 && !ctl[CTL_DONE]) {
+        const int t = *T;
+        ctl[CTL_NB] += t;
+        ctl[CTL_FIN] += *fin_total;
+        ctl[CTL_S] = 2 * t;
+        if (level == 0) ctl[CTL_ROOT_SPLIT] = t > 0;
+        if (t > 0) ctl[CTL_SCATTERS] += 1;
+        else { ctl[CTL_DONE] = 1; ctl[CTL_LEVELS] = level; }
+    }
     if (*T == 0) return;
     __shared__ unsigned wtot[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -201,30 +213,16 @@ __global__ void __launch_bounds__(1024) k_part_carry(unsigned *__restrict__ tsum
     }
 }
 
-// End of a level: advance the control block (one thread).
-__global__ void k_level_end(int *ctl, const int *__restrict__ split_total, const int *__restrict__ fin_total,
-                            int level) {
-    if (ctl[CTL_DONE]) return;
-    const int T = *split_total;
-    ctl[CTL_NB] += T;
-    ctl[CTL_FIN] += *fin_total;
-    ctl[CTL_S] = 2 * T;
-    if (level == 0) ctl[CTL_ROOT_SPLIT] = T > 0;
-    if (T > 0) ctl[CTL_SCATTERS] += 1;
-    else { ctl[CTL_DONE] = 1; ctl[CTL_LEVELS] = level; }
-}
-
 // Decide, per segment, leaf or split; for a split pick the widest dimension
 // of the tight box (lowest index on ties) and its midpoint.
 template <int DC>
-__global__ void k_classify(int S_max, const int *__restrict__ ctl, const int *__restrict__ start, const int *__restrict__ end,
-                           const int *__restrict__ depth, const int *__restrict__ lo,
-                           const int *__restrict__ hi, int leaf, int depth_cap, int fin_threshold,
-                           int *__restrict__ split_flag, int *__restrict__ fin_flag, int *__restrict__ sdim,
-                           float *__restrict__ sval) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S_max) return;
-    if (ctl[CTL_DONE] || s >= ctl[CTL_S]) {   // padding up to the launch bound (or loop over)
+__device__ __forceinline__ void classify_seg(int s, bool live, const int *__restrict__ start,
+                                             const int *__restrict__ end, const int *__restrict__ depth,
+                                             const int *__restrict__ lo, const int *__restrict__ hi, int leaf,
+                                             int depth_cap, int fin_threshold, int *__restrict__ split_flag,
+                                             int *__restrict__ fin_flag, int *__restrict__ sdim,
+                                             float *__restrict__ sval) {
+    if (!live) {   // padding up to the launch bound (or loop over)
         split_flag[s] = 0;
         fin_flag[s] = 0;
         return;
@@ -256,10 +254,22 @@ __global__ void k_classify(int S_max, const int *__restrict__ ctl, const int *__
     sval[s] = bv;
 }
 
+template <int DC>
+__global__ void k_classify(int S_max, const int *__restrict__ ctl, const int *__restrict__ start, const int *__restrict__ end,
+                           const int *__restrict__ depth, const int *__restrict__ lo,
+                           const int *__restrict__ hi, int leaf, int depth_cap, int fin_threshold,
+                           int *__restrict__ split_flag, int *__restrict__ fin_flag, int *__restrict__ sdim,
+                           float *__restrict__ sval) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S_max) return;
+    classify_seg<DC>(s, !ctl[CTL_DONE] && s < ctl[CTL_S], start, end, depth, lo, hi, leaf, depth_cap,
+                     fin_threshold, split_flag, fin_flag, sdim, sval);
+}
+
 // Write each segment into its parent's child slot (tight box + reference),
 // record split nodes and prepare the next level's child segments.
 template <int DC>
-__global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__restrict__ start, const int *__restrict__ end,
+__device__ __forceinline__ void link_seg(int s, const int *__restrict__ ctl, const int *__restrict__ start, const int *__restrict__ end,
                        const int *__restrict__ parent, const int *__restrict__ side,
                        const int *__restrict__ depth, const int *__restrict__ lo, const int *__restrict__ hi,
                        const int *__restrict__ split_flag, const int *__restrict__ split_rank,
@@ -269,8 +279,6 @@ __global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__rest
                        int *__restrict__ nx_depth, int *__restrict__ nx_lo, int *__restrict__ nx_hi,
                        const int *__restrict__ fin_flag, const int *__restrict__ fin_rank, Segs fin,
                        int *__restrict__ n_parent, int *__restrict__ roots, int fin_link) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S_max || ctl[CTL_DONE] || s >= ctl[CTL_S]) return;
     const int node_base = ctl[CTL_NB], fin_base = ctl[CTL_FIN];
     const int st = start[s], size = end[s] - st;
     const int p = parent[s];
@@ -344,6 +352,124 @@ __global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__rest
             }
         }
     }
+}
+
+template <int DC>
+__global__ void k_link(int S_max, const int *__restrict__ ctl, const int *__restrict__ start, const int *__restrict__ end,
+                       const int *__restrict__ parent, const int *__restrict__ side,
+                       const int *__restrict__ depth, const int *__restrict__ lo, const int *__restrict__ hi,
+                       const int *__restrict__ split_flag, const int *__restrict__ split_rank,
+                       const int *__restrict__ sdim, const float *__restrict__ sval,
+                       float4 *__restrict__ nodes, int *__restrict__ n_sdim, float *__restrict__ n_sval,
+                       int2 *__restrict__ n_range, int *__restrict__ nx_parent, int *__restrict__ nx_side,
+                       int *__restrict__ nx_depth, int *__restrict__ nx_lo, int *__restrict__ nx_hi,
+                       const int *__restrict__ fin_flag, const int *__restrict__ fin_rank, Segs fin,
+                       int *__restrict__ n_parent, int *__restrict__ roots, int fin_link) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S_max || ctl[CTL_DONE] || s >= ctl[CTL_S]) return;
+    link_seg<DC>(s, ctl, start, end, parent, side, depth, lo, hi, split_flag, split_rank, sdim, sval, nodes, n_sdim, n_sval, n_range, nx_parent, nx_side, nx_depth, nx_lo, nx_hi, fin_flag, fin_rank, fin, n_parent, roots, fin_link);
+}
+
+// One block does a whole level's segment work when the level has at most
+// kHeadMax segment slots: classify, the two exclusive scans (split and
+// finisher flags, totals at index S_max) and link, with block barriers
+// instead of eight kernel boundaries.
+constexpr int HEAD_NT = 1024;
+constexpr int kHeadMax = 16384;
+
+// Exclusive scan of in[0, n) into out[0, n], out[n] = total, by one block.
+__device__ void block_excl_scan(const int *in, int *out, int n, int *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = (n + HEAD_NT - 1) / HEAD_NT;
+    const int i0 = min(n, threadIdx.x * per), i1 = min(n, i0 + per);
+    int t = 0;
+    for (int i = i0; i < i1; ++i) t += in[i];
+    int x = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int run = (warp ? wsum[warp - 1] : 0) + x - t;
+    for (int i = i0; i < i1; ++i) {
+        const int v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == HEAD_NT - 1) out[n] = wsum[31];
+    __syncthreads();
+}
+
+template <int DC>
+__global__ void __launch_bounds__(HEAD_NT) k_level_head(
+    int S_max, const int *__restrict__ ctl, const int *__restrict__ start, const int *__restrict__ end,
+    const int *__restrict__ parent, const int *__restrict__ side, const int *__restrict__ depth,
+    const int *__restrict__ lo, const int *__restrict__ hi, int leaf, int depth_cap, int fin_threshold,
+    int *__restrict__ split_flag, int *__restrict__ split_rank, int *__restrict__ sdim, float *__restrict__ sval,
+    float4 *__restrict__ nodes, int *__restrict__ n_sdim, float *__restrict__ n_sval, int2 *__restrict__ n_range,
+    int *__restrict__ nx_parent, int *__restrict__ nx_side, int *__restrict__ nx_depth, int *__restrict__ nx_lo,
+    int *__restrict__ nx_hi, int *__restrict__ fin_flag, int *__restrict__ fin_rank, Segs fin,
+    int *__restrict__ n_parent, int *__restrict__ roots, int fin_link) {
+    __shared__ int wsum[32];
+    const int S = ctl[CTL_DONE] ? 0 : min(ctl[CTL_S], S_max);
+    for (int x = threadIdx.x; x < S_max; x += HEAD_NT)
+        classify_seg<DC>(x, x < S, start, end, depth, lo, hi, leaf, depth_cap, fin_threshold, split_flag, fin_flag,
+                         sdim, sval);
+    __syncthreads();
+    block_excl_scan(split_flag, split_rank, S_max, wsum);
+    block_excl_scan(fin_flag, fin_rank, S_max, wsum);
+    for (int x = threadIdx.x; x < S; x += HEAD_NT)
+        link_seg<DC>(x, ctl, start, end, parent, side, depth, lo, hi, split_flag, split_rank, sdim, sval, nodes,
+                     n_sdim, n_sval, n_range, nx_parent, nx_side, nx_depth, nx_lo, nx_hi, fin_flag, fin_rank, fin,
+                     n_parent, roots, fin_link);
+}
+
+// Enqueue one level's segment work: the one-block head when the level has
+// few enough segment slots, else classify + two device-wide scans + link.
+// scan_ws (may be NULL) is workspace for the scans (scan_ws_words(S_max)).
+template <int DC>
+pg_status level_segments(int S_max, int *ctl, const Segs &cur, const Segs &nxt, int leaf, int thr, int *split_flag,
+                         int *split_rank, int *sdim, float *sval, int *fin_flag, int *fin_rank, const Segs &fin,
+                         float4 *nodes, int *n_sdim, float *n_sval, int2 *n_range, int *n_parent, int *roots,
+                         int fin_link, int *scan_ws, cudaStream_t s) {
+    if (S_max <= kHeadMax) {
+        k_level_head<DC><<<1, HEAD_NT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth,
+                                               cur.lo, cur.hi, leaf, PG_DEPTH_CAP, thr, split_flag, split_rank,
+                                               sdim, sval, nodes, n_sdim, n_sval, n_range, nxt.parent, nxt.side,
+                                               nxt.depth, nxt.lo, nxt.hi, fin_flag, fin_rank, fin, n_parent, roots,
+                                               fin_link);
+        count_launch();
+        return PG_OK;
+    }
+    const int gs = ceil_div_i(S_max, BT);
+    k_classify<DC><<<gs, BT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.depth, cur.lo, cur.hi, leaf, PG_DEPTH_CAP,
+                                     thr, split_flag, fin_flag, sdim, sval);
+    count_launch();
+    if (scan_ws) {
+        PG_TRY(exclusive_scan_ws(split_flag, split_rank, S_max, scan_ws, s));
+        PG_TRY(exclusive_scan_ws(fin_flag, fin_rank, S_max, scan_ws, s));
+    } else {
+        PG_TRY(exclusive_scan(split_flag, split_rank, S_max, s));
+        PG_TRY(exclusive_scan(fin_flag, fin_rank, S_max, s));
+    }
+    k_link<DC><<<gs, BT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo, cur.hi,
+                                 split_flag, split_rank, sdim, sval, nodes, n_sdim, n_sval, n_range, nxt.parent,
+                                 nxt.side, nxt.depth, nxt.lo, nxt.hi, fin_flag, fin_rank, fin, n_parent, roots,
+                                 fin_link);
+    count_launch();
+    return PG_OK;
 }
 
 // Move every point of a split segment to its child range (see k_part_tiles)
@@ -649,20 +775,12 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     int level = 0;
     for (; level <= PG_DEPTH_CAP + 1; ++level) {
         const int S_max = (int)std::min<int64_t>((int64_t)1 << std::min(level, 30), seg_cap);
-        const int gs = ceil_div_i(S_max, BT);
-        k_classify<DC><<<gs, BT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.depth, cur.lo, cur.hi, leaf,
-                                         PG_DEPTH_CAP, fin_max, split_flag, fin_flag, sdim, sval);
-        count_launch();
-        PG_TRY(exclusive_scan(split_flag, split_rank, S_max, s));
-        PG_TRY(exclusive_scan(fin_flag, fin_rank, S_max, s));
-        k_link<DC><<<gs, BT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo,
-                                     cur.hi, split_flag, split_rank, sdim, sval, t->nodes, t->split_dim,
-                                     t->split_val, t->node_range, nxt.parent, nxt.side, nxt.depth, nxt.lo, nxt.hi,
-                                     fin_flag, fin_rank, fin, t->parent, nullptr, 0);
-        count_launch();
+        PG_TRY(level_segments<DC>(S_max, ctl, cur, nxt, leaf, fin_max, split_flag, split_rank, sdim, sval, fin_flag,
+                                  fin_rank, fin, t->nodes, t->split_dim, t->split_val, t->node_range, t->parent,
+                                  nullptr, 0, nullptr, s));
         const int *T = split_rank + S_max;
         k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<unsigned>());
-        k_part_carry<<<1, 1024, 0, s>>>(sBsum.as<unsigned>(), ntiles, T);
+        k_part_carry<<<1, 1024, 0, s>>>(sBsum.as<unsigned>(), ntiles, T, ctl, fin_rank + S_max, level);
         count_launch();
         count_launch();
         {
@@ -672,8 +790,6 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
                                                      nxt.lo, nxt.hi, T);
             count_launch();
         }
-        k_level_end<<<1, 1, 0, s>>>(ctl, T, fin_rank + S_max, level);
-        count_launch();
         PG_TRY(check_launch("build level"));
         std::swap(P, Q);
         std::swap(seg_of, seg_of_nx);
@@ -786,26 +902,16 @@ pg_status forest_levels_impl(const ForestArgs &fa, cudaStream_t s) {
     count_launch();
     for (int level = 0; level < fa.levels; ++level) {
         const int S_max = (int)std::min<int64_t>((int64_t)fa.ntrees << std::min(level, 30), seg_cap);
-        const int gs = ceil_div_i(S_max, BT);
         const int thr = level == fa.levels - 1 ? INT_MAX : fa.fin_max;
-        k_classify<DC><<<gs, BT, 0, s>>>(S_max, fa.ctl, cur.start, cur.end, cur.depth, cur.lo, cur.hi, fa.leaf,
-                                         PG_DEPTH_CAP, thr, split_flag, fin_flag, sdim, sval);
-        count_launch();
-        PG_TRY(exclusive_scan_ws(split_flag, split_rank, S_max, fa.scan_ws, s));
-        PG_TRY(exclusive_scan_ws(fin_flag, fin_rank, S_max, fa.scan_ws, s));
-        k_link<DC><<<gs, BT, 0, s>>>(S_max, fa.ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth, cur.lo,
-                                     cur.hi, split_flag, split_rank, sdim, sval, fa.nodes, fa.n_sdim, fa.n_sval,
-                                     fa.n_range, nxt.parent, nxt.side, nxt.depth, nxt.lo, nxt.hi, fin_flag,
-                                     fin_rank, fin, fa.n_parent, fa.roots, 1);
-        count_launch();
+        PG_TRY(level_segments<DC>(S_max, fa.ctl, cur, nxt, fa.leaf, thr, split_flag, split_rank, sdim, sval, fin_flag,
+                                  fin_rank, fin, fa.nodes, fa.n_sdim, fa.n_sval, fa.n_range, fa.n_parent, fa.roots, 1,
+                                  fa.scan_ws, s));
         const int *T = split_rank + S_max;
         k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(fa.n, P, seg_of, split_flag, sdim, sval, T, fa.tiles);
-        k_part_carry<<<1, 1024, 0, s>>>(fa.tiles, ntiles, T);
+        k_part_carry<<<1, 1024, 0, s>>>(fa.tiles, ntiles, T, fa.ctl, fin_rank + S_max, level);
         k_part<DC><<<ntiles, PT_THREADS, 0, s>>>(fa.n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
                                                  split_rank, sdim, sval, fa.tiles, nxt.start, nxt.end, nxt.lo,
                                                  nxt.hi, T);
-        k_level_end<<<1, 1, 0, s>>>(fa.ctl, T, fin_rank + S_max, level);
-        count_launch();
         count_launch();
         count_launch();
         count_launch();
