@@ -610,14 +610,15 @@ constexpr size_t kFinSmemBudget = 110 * 1024;   // shared memory of a finisher b
 template <int DC>
 __global__ void __launch_bounds__(FIN_NT, 2) k_finish(Segs fin, float4 *P, int leaf, int ns, int sc, const int *ctl,
                                                       float4 *nodes, int *n_sdim, float *n_sval, int2 *n_range,
-                                                      int *root_rec, int *depth_max, int *n_parent) {
+                                                      int *root_rec, int *depth_max, int *n_parent,
+                                                      int *leaf_parent) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int f = blockIdx.x;
     const int nb = ctl[CTL_NB];
     const int st = fin.start[f], en = fin.end[f];
     const CtaTree r = cta_build_smem<DC, FIN_NT>(P, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC, smem, ns,
                                                  sc, leaf, nb + st, nodes, n_sdim, n_sval, n_range, fin.depth[f],
-                                                 n_parent, nullptr,
+                                                 n_parent, leaf_parent,
                                                  fin.parent[f] >= 0 ? 2 * fin.parent[f] + fin.side[f] : -1);
     if (threadIdx.x == 0) {
         const int p = fin.parent[f];
@@ -741,6 +742,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     int *seg_of = sSeg0.as<int>(), *seg_of_nx = sSeg1.as<int>();
     PG_CUDA(cudaMemsetAsync(seg_of, 0, sizeof(int) * (size_t)n, s));   // all in segment 0
     if (!t->leaf_parent) PG_TRY(dalloc_n(&t->leaf_parent, (size_t)n, s));
+    PG_CUDA(cudaMemsetAsync(t->leaf_parent, 0xff, sizeof(int) * (size_t)n, s));   // a leaf root keeps -1
     // Segments of up to fin_max points are finished in one block's shared memory.
     const int fin_max = smem_build_points(DC, leaf, kFinSmemBudget);
     const int fin_sc = smem_seg_cap(fin_max, leaf);
@@ -818,7 +820,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
             KTimer kt("build_finish", s);
             k_finish<DC><<<fin_total, FIN_NT, fin_smem, s>>>(fin, P, leaf, fin_max, fin_sc, ctl, t->nodes,
                                                              t->split_dim, t->split_val, t->node_range, rec, rec + 2,
-                                                             t->parent);
+                                                             t->parent, t->leaf_parent);
             count_launch();
         }
         PG_TRY(check_launch("build finish"));
@@ -830,9 +832,10 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
             t->root_cnt = h[1];
         }
     }
-    PG_CUDA(cudaMemsetAsync(t->leaf_parent, 0xff, sizeof(int) * (size_t)n, s));
-    if (t->num_nodes > 0) {
-        k_leaf_parents<DC><<<ceil_div_i(t->num_nodes, BT), BT, 0, s>>>(t->nodes, t->num_nodes, t->leaf_parent);
+    // leaves of finisher segments were recorded by the finisher; the level
+    // nodes' leaf children are recorded here
+    if (nb > 0) {
+        k_leaf_parents<DC><<<ceil_div_i(nb, BT), BT, 0, s>>>(t->nodes, nb, t->leaf_parent);
         count_launch();
     }
     // The final array becomes the bucket; the other ping-pong buffer is freed.
