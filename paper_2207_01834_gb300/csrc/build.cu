@@ -104,7 +104,7 @@ enum { CTL_S = 0, CTL_NB, CTL_FIN, CTL_DONE, CTL_SCATTERS, CTL_LEVELS, CTL_ROOT_
 //                 so no segment total is needed before the move; the last
 //                 point of a segment writes the two children's ranges.
 // A segment start is a position whose segment differs from the previous one.
-constexpr int PT_THREADS = 256, PT_ROWS = 16, PT_TILE = PT_THREADS * PT_ROWS, PT_WARPS = PT_THREADS / 32;
+constexpr int PT_THREADS = 256, PT_ROWS = 8, PT_TILE = PT_THREADS * PT_ROWS, PT_WARPS = PT_THREADS / 32;
 constexpr int kBoxSlots = 16;   // children whose boxes a tile reduces in shared memory
 
 // Segmented count: `has` a segment start, `cnt` flags after the last start.
