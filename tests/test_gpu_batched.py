@@ -100,6 +100,29 @@ def test_batched_deep_cloud_takes_the_global_memory_finisher(api):
                           dba.cpu().numpy(), loss.cpu().numpy(), rows_per_pair=600)
 
 
+def test_batched_many_small_clouds_take_the_multi_kernel_level_path(api):
+    """16,600 clouds: the forest's first level has more segment slots than one
+    block handles (16,384), so it runs as classify + device-wide scans + link."""
+    rng = np.random.default_rng(41)
+    npairs, k = 8300, 4
+    sa = rng.integers(1, 40, npairs)
+    sb = rng.integers(1, 40, npairs)
+    a = rng.random((int(sa.sum()), 3)).astype(np.float32)
+    b = rng.random((int(sb.sum()), 3)).astype(np.float32)
+    a_off = np.concatenate([[0], np.cumsum(sa)])
+    b_off = np.concatenate([[0], np.cumsum(sb)])
+    loss, iab, iba, dab, dba = api.pg_batched_chamfer(_cuda(a), a_off, _cuda(b), b_off, k, want_dist=True)
+    iab, iba, dab, dba, loss = (t.cpu().numpy() for t in (iab, iba, dab, dba, loss))
+    for i in np.sort(rng.choice(npairs, 300, replace=False)):
+        A, B = a[a_off[i]:a_off[i + 1]], b[b_off[i]:b_off[i + 1]]
+        oi, od = oracle.knn(B, A, k, nthreads=0)
+        compare_knn(iab[a_off[i]:a_off[i + 1]], dab[a_off[i]:a_off[i + 1]], oi, od, B, A)
+        oi, od = oracle.knn(A, B, k, nthreads=0)
+        compare_knn(iba[b_off[i]:b_off[i + 1]], dba[b_off[i]:b_off[i + 1]], oi, od, A, B)
+        want = oracle.chamfer(A, [0, len(A)], B, [0, len(B)], k)[0][0]
+        assert abs(float(loss[i]) - want) <= 1e-5 * max(want, 1e-30), (i, float(loss[i]), want)
+
+
 def test_batched_tiny_clouds_and_padding(api):
     a = synth.uniform(1 + 3 + 40, 3, 11)
     b = synth.uniform(2 + 1 + 17, 3, 12)
