@@ -43,8 +43,11 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--leaf", type=int, default=0, help="leaf size (0: autotuned)")
-    p.add_argument("--variant", type=int, default=0, help="traversal: 0 auto, 1 thread per query, 2 warp packets")
+    # defaults: the configuration autotune.best_config picks for this workload on GB300 (leaf 48 and
+    # the postponed-leaf traversal; leaf 64 is within 1%); 0 re-tunes at run time
+    p.add_argument("--leaf", type=int, default=48, help="leaf size (0: autotuned)")
+    p.add_argument("--variant", type=int, default=3,
+                   help="traversal: 0 autotuned, 1 thread per query, 2 warp packets, 3 postponed leaves")
     p.add_argument("--n", type=int, default=N_POINTS, help=argparse.SUPPRESS)
     p.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
