@@ -567,10 +567,28 @@ def run_ours(args):
     knn_avg_ms = knn_ms / max(knn_launches, 1)
     achieved = alg_bytes / (knn_avg_ms / 1e3) / 1e9
     sha = kernel_sha(KNN_SOURCES)
+    traffic = traffic_for("knn_traverse", sha, n, variant, leaf)
+    # touched-bytes model: node records and bucket entries the traversal loads
+    # (through L1/L2), counted by the counting instance of the same kernel in
+    # one extra launch outside the timed region
+    touched = None
+    if variant == 3:
+        t = api.pg_tree_build(x, leaf_size=leaf)
+        api.pg_knn_touch_read()
+        api.pg_knn_touch_enable(True)
+        api.pg_knn(t, None, K, out_idx=idx, out_dist=dst)
+        api.pg_knn_touch_enable(False)
+        nrec, nent = api.pg_knn_touch_read()
+        t.free()
+        touched = nrec * 16 * (DIM + 1) + nent * 16 * ((DIM + 1 + 3) // 4)
     roofline = {"bound": "hbm", "kernel": f"{KNN_KERNELS.get(variant, 'k_knn')}<3,10> (knn_traverse)",
                 "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_for("knn_traverse", sha, n, variant, leaf), "alg_bytes_per_launch": alg_bytes,
+                "traffic": traffic,
+                "traffic_frac": None if traffic is None else traffic / (knn_avg_ms / 1e3) / 1e9 / peak,
+                "touched_bytes_per_launch": touched,
+                "touched_frac": None if touched is None else touched / (knn_avg_ms / 1e3) / 1e9 / peak,
+                "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": knn_avg_ms, "launches_timed": knn_launches, "source_sha": sha}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

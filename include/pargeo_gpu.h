@@ -143,6 +143,20 @@ PG_API pg_status pg_tree_export(const pg_tree *tree, float *nodes, int32_t *spli
  */
 PG_API pg_status pg_knn_set_variant(int variant);
 
+/*
+ * Touched-bytes counters of the traversal (measurement only; no counterpart in
+ * the paper).  While enabled (on != 0), every later variant-3 launch in this
+ * process runs an instance of the same kernel that also counts, over all its
+ * queries, the node records and the bucket entries it loads; the answer is
+ * unchanged.  pg_knn_touch_read synchronises the device, returns the counts
+ * accumulated since the last read (zeros if nothing was counted) and resets
+ * them.  Bytes: node_records * 16 * (DC + 1), bucket_entries * 16 *
+ * ceil((DC + 1) / 4), DC the dimension class.  The counters live on the device
+ * current at the first counted launch.  Errors: PG_EINVAL for NULL outputs.
+ */
+PG_API pg_status pg_knn_touch_enable(int on);
+PG_API pg_status pg_knn_touch_read(int64_t *node_records, int64_t *bucket_entries);
+
 /* ------------------------------------------------------------------------
  * BDL-tree (paper Section 5; Appendix A.2 Insert_L, A.3 Erase_L, A.4 kNN_L).
  * A forest of static kd-trees in slots i = 0, 1, ... with capacity

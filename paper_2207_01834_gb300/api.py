@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import PgError, TreeInfo, call
 
 __all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_knn", "pg_tree_free", "pg_tree_info",
-           "pg_tree_export", "pg_knn_set_variant", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
+           "pg_tree_export", "pg_knn_set_variant", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
            "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_knn_backward_noalloc",
            "pg_batched_chamfer",
            "pg_batched_chamfer_backward", "launch_count", "profile_enable", "profile_read", "version",
@@ -133,8 +133,20 @@ def pg_tree_export(tree: Tree) -> dict:
 
 
 def pg_knn_set_variant(variant: int) -> None:
-    """0 automatic, 1 thread per query, 2 warp packets (process-wide)."""
+    """0 automatic, 1 thread per query, 2 warp packets, 3 postponed leaves (process-wide)."""
     call("pg_knn_set_variant", variant)
+
+
+def pg_knn_touch_enable(on: bool = True) -> None:
+    """Count node records and bucket entries loaded by later variant-3 launches."""
+    call("pg_knn_touch_enable", 1 if on else 0)
+
+
+def pg_knn_touch_read() -> tuple[int, int]:
+    """(node records, bucket entries) loaded since the last read; resets them."""
+    a, b = C.c_int64(), C.c_int64()
+    call("pg_knn_touch_read", C.byref(a), C.byref(b))
+    return int(a.value), int(b.value)
 
 
 # ---------------------------------------------------------------- BDL forest

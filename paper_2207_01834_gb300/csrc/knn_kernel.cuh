@@ -183,9 +183,9 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
 // insertions then run converged (as many rounds as the busiest lane needs).
 // Each lane's pruning uses only its own k-th distance, so the answer is the
 // same exact k-NN as the other variants.
-template <int DC, int KC, bool NC = true>
+template <int DC, int KC, bool NC = true, bool COUNT = false>
 __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict__ bucket, int lref, int lcnt,
-                                                        const float *q, KList<KC> &L) {
+                                                        const float *q, KList<KC> &L, unsigned &cand) {
     const int maxc = __reduce_max_sync(0xffffffffu, lcnt);
     for (int base = 0; base < maxc; base += 32) {
         const int n = min(32, maxc - base);
@@ -196,6 +196,7 @@ __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict
                 float p[DC];
                 unsigned pid;
                 load_point<DC, NC>(bucket, lref + base + j, p, pid);
+                if (COUNT) ++cand;
                 const float dd = sqdist<DC>(q, p);
                 mask |= (pair_key(dd, pid) < kk ? 1u : 0u) << j;
             }
@@ -208,13 +209,17 @@ __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict
             float p[DC];
             unsigned pid;
             load_point<DC, NC>(bucket, act ? lref + base + j : lref, p, pid);
+            if (COUNT && act) ++cand;
             L.offer_pred(sqdist<DC>(q, p), pid, act);
         }
     }
 }
 
-template <int DC, int KC, bool NC = true>
-__device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q, bool valid, KList<KC> &L) {
+// COUNT: also count, per lane, the node records and bucket entries it loads
+// (the touched-bytes model of the traversal; a separate instantiation).
+template <int DC, int KC, bool NC = true, bool COUNT = false>
+__device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q, bool valid, KList<KC> &L,
+                                               unsigned &nrec, unsigned &cand) {
     constexpr int NW = node_w(DC);
     int s_ref[KNN_STACK], s_cnt[KNN_STACK];
     float s_d[KNN_STACK];
@@ -247,6 +252,7 @@ __device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q
                     }
                 }
                 if (ref >= 0) {
+                    if (COUNT) ++nrec;
                     float rec[4 * NW];
                     const float4 *np = T.nodes + (size_t)ref * NW;
 #pragma unroll
@@ -276,17 +282,18 @@ __device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q
         }
         if (!__any_sync(0xffffffffu, lcnt > 0)) break;
         // leaf phase, converged
-        scan_own_leaf_converged<DC, KC, NC>(T.bucket, lref, lcnt, q, L);
+        scan_own_leaf_converged<DC, KC, NC, COUNT>(T.bucket, lref, lcnt, q, L, cand);
         lcnt = 0;
     }
 }
 
-template <int DC, int KC>
+template <int DC, int KC, bool COUNT = false>
 __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restrict__ trees, int ntrees,
                                                         const float *__restrict__ queries,
                                                         const float4 *__restrict__ self_bucket,
                                                         const int32_t *__restrict__ order, int64_t m, int dim, int k,
-                                                        int32_t *__restrict__ out_idx, float *__restrict__ out_dist) {
+                                                        int32_t *__restrict__ out_idx, float *__restrict__ out_dist,
+                                                        unsigned long long *__restrict__ touch = nullptr) {
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = pos < m;
     float q[DC];
@@ -306,7 +313,20 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
     }
     KList<KC> L;
     L.init(k);
-    for (int t = 0; t < ntrees; ++t) search_tree_ww<DC, KC>(trees[t], q, valid, L);
+    unsigned nrec = 0, cand = 0;
+    for (int t = 0; t < ntrees; ++t) search_tree_ww<DC, KC, true, COUNT>(trees[t], q, valid, L, nrec, cand);
+    if (COUNT) {
+        unsigned long long a = nrec, b = cand;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(touch, a);
+            atomicAdd(touch + 1, b);
+        }
+    }
     if (!valid) return;
     int32_t *oi = out_idx + row * k;
     float *od = out_dist + row * k;
@@ -667,6 +687,9 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
         else if (variant == 3)                                                                             \
             k_knn_ww<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(                         \
                 trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist);                 \
+        else if (variant == 4)                                                                             \
+            k_knn_ww<DCN, KCN, true><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(                   \
+                trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, touch);          \
         else                                                                                               \
             k_knn_packet<DCN, KCN><<<ceil_div_i(m, PKT_THREADS), PKT_THREADS, 0, s>>>(                     \
                 trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist);                 \
@@ -676,7 +699,8 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
     namespace pg {                                                                                         \
     pg_status knn_launch_dc##DCN(const TreeDesc *trees, int ntrees, const float *queries,                  \
                                  const float4 *self_bucket, const int32_t *order, int64_t m, int dim,      \
-                                 int k, int32_t *out_idx, float *out_dist, int variant, cudaStream_t s) {  \
+                                 int k, int32_t *out_idx, float *out_dist, int variant,                    \
+                                 unsigned long long *touch, cudaStream_t s) {                              \
         KTimer kt("knn_traverse", s);                                                                      \
         switch (k_class(k)) {                                                                              \
             PG_KNN_CASE(DCN, 1)                                                                            \

@@ -160,6 +160,32 @@ def test_variants_agree_bitwise(api):
             assert torch.equal(a, b)
 
 
+def test_touch_counting_instance_same_answer(api):
+    """The counting instance of the postponed-leaf traversal returns the same
+    bits, and its counts are plausible: every query loads at least k bucket
+    entries (its list must fill) and at most two loads per entry (test and
+    insertion), and a read resets them."""
+    pts = synth.gmm(40000, 3, 43)
+    k = 10
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=32)
+    api.pg_knn_set_variant(3)
+    try:
+        ref = api.pg_knn(tree, None, k)
+        api.pg_knn_touch_read()
+        api.pg_knn_touch_enable(True)
+        got = api.pg_knn(tree, None, k)
+        api.pg_knn_touch_enable(False)
+        nrec, nent = api.pg_knn_touch_read()
+        assert api.pg_knn_touch_read() == (0, 0)
+    finally:
+        api.pg_knn_touch_enable(False)
+        api.pg_knn_set_variant(0)
+    assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])
+    n = len(pts)
+    assert n * k <= nent <= 2 * n * n
+    assert n <= nrec <= n * tree.info().num_nodes
+
+
 def test_knn_deterministic_and_stream(api):
     pts = synth.gmm(50000, 3, 31)
     s = torch.cuda.Stream()
