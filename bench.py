@@ -297,6 +297,19 @@ def other_configs(api, torch, dev):
     bms = timed(b2)
     qms = timed(q2)
     out["2d_20k_k5"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 20000 / qms / 1e3}
+    # k-NN graph of 10,000,000 uniform 2D points, k = 10 (the paper's Table 1
+    # k-NN graph workload is 2D 10M; its k is not stated)
+    xg = torch.from_numpy(synth.uniform(10_000_000, 2, synth.BASE_SEED + 9)).to(dev)
+    hg = {}
+
+    def graph():
+        t = api.pg_tree_build(xg, 32)
+        hg["e"] = api.pg_knn_graph(t, 10)
+        t.free()
+
+    gms = timed(graph)
+    out["knn_graph_2d_10m_k10"] = {"build_and_graph_ms": gms, "edges": int(hg["e"].shape[0])}
+    del xg, hg
     # 5D / 7D clustered: 2,000,000 points, 1,000,000 separate queries, k = 16
     # (leaf size and traversal variant autotuned on the workload itself)
     from paper_2207_01834_gb300 import autotune

@@ -131,6 +131,26 @@ PG_API pg_status pg_tree_export(const pg_tree *tree, float *nodes, int32_t *spli
                          float *bucket);
 
 /*
+ * k-NN graph of the tree's points (paper Section 4, geometric graph
+ * generators: the k-NN graph comes from the kd-tree's k-NN search).  Point i is
+ * joined to its k nearest OTHER points, i.e. the k smallest (squared distance,
+ * row) pairs over rows != i; edges are undirected, each listed once as
+ * (u, v) with u < v, all sorted by (u, v).  Rows are the tree's input rows.
+ *   k          1..63.
+ *   capacity   edges out_edges can hold (int32 pairs); n * k always suffices.
+ *   out_edges  device, 2 * capacity int32 (u0, v0, u1, v1, ...), or NULL to
+ *              only count.
+ *   out_count  host: the number of edges (written even when the edges are
+ *              not, so a caller can size a second call).
+ * Stream-ordered; synchronises the stream once to read the count.  Errors:
+ * PG_EINVAL (NULL tree/out_count, k or capacity out of range, n * k >= 2^31,
+ * or capacity below the edge count with out_edges given: nothing written);
+ * PG_ENOMEM for scratch (about 40 * n * k bytes).
+ */
+PG_API pg_status pg_knn_graph(const pg_tree *tree, int k, int64_t capacity, int32_t *out_edges,
+                              int64_t *out_count, void *stream);
+
+/*
  * Traversal variant used by pg_knn and pg_bdl_knn for every later call in this
  * process (App. A.1.3 searches each query independently; every variant returns
  * that same exact answer): 1 = one thread per query walks its own path;

@@ -17,6 +17,11 @@ Contents
                  Erase_L, Section 5 "Parallel Batch Insertion", Appendix A.2-A.3)
                  and its live point set.
   kdtree_check   checker of the kd-tree invariants (Section 5 intro).
+  knn_graph      the k-NN graph (Section 4, geometric graph generators: the
+                 k-NN graph comes from the kd-tree's k-NN search): every point
+                 joined to its k nearest other points, undirected edges listed
+                 once as (u, v), u < v, sorted.  The paper does not say whether
+                 edges are directed; this oracle takes the symmetrised reading.
 
 Every float computation here is float64 on float32 inputs.
 """
@@ -173,3 +178,29 @@ def chamfer(a, a_off, b, b_off, k: int, nthreads: int = 1):
         gb[b_off[i]:b_off[i + 1]] += gq
         ga[a_off[i]:a_off[i + 1]] += gp
     return loss, idx_ab, idx_ba, ga, gb
+
+
+def knn_graph(points, k: int, nthreads: int = 1) -> np.ndarray:
+    """k-NN graph of `points` as an (E, 2) int64 array of edges (u, v), u < v,
+    in ascending (u, v) order (Section 4, geometric graph generators).
+
+    Step by step, from the definitions: the k nearest other points of i are
+    the k smallest (distance, index) pairs over indices j != i; an undirected
+    edge {i, j} exists when j is among i's k or i among j's k.
+    """
+    p = np.asarray(points, np.float32)
+    n = len(p)
+    if n < 2:
+        return np.zeros((0, 2), np.int64)
+    idx, _ = knn(p, p, min(k + 1, n), nthreads=nthreads)
+    edges = set()
+    for i in range(n):
+        others = [int(t) for t in idx[i] if t >= 0 and t != i]
+        if len(others) > k:          # i itself was not among its k + 1
+            others = others[:k]
+        for j in others[:k]:
+            edges.add((min(i, j), max(i, j)))
+    if not edges:
+        return np.zeros((0, 2), np.int64)
+    return np.array(sorted(edges), np.int64)
+

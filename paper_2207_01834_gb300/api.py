@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import PgError, TreeInfo, call
 
 __all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_knn", "pg_tree_free", "pg_tree_info",
-           "pg_tree_export", "pg_knn_set_variant", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
+           "pg_tree_export", "pg_knn_graph", "pg_knn_set_variant", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
            "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_knn_backward_noalloc",
            "pg_batched_chamfer",
            "pg_batched_chamfer_backward", "launch_count", "profile_enable", "profile_read", "version",
@@ -130,6 +130,17 @@ def pg_tree_export(tree: Tree) -> dict:
             "root_lo": np.array(info.root_lo[:info.dim], np.float32),
             "root_hi": np.array(info.root_hi[:info.dim], np.float32), "num_nodes": nn,
             "depth": info.depth, "leaf_size": info.leaf_size}
+
+
+def pg_knn_graph(tree: Tree, k: int, stream=None) -> torch.Tensor:
+    """Undirected k-NN graph of the tree's points: (E, 2) int32 device tensor of
+    edges (u, v), u < v, sorted; point i is joined to its k nearest other points."""
+    n = tree.n
+    cap = max(1, n * k)
+    out = torch.empty((cap, 2), dtype=torch.int32, device=tree.device)
+    cnt = C.c_int64()
+    call("pg_knn_graph", tree.handle, k, cap, _ptr(out), C.byref(cnt), _stream(stream))
+    return out[:cnt.value]
 
 
 def pg_knn_set_variant(variant: int) -> None:

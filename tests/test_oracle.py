@@ -220,3 +220,49 @@ def test_chamfer_grad_matches_torch_autograd():
     assert abs(float(total.detach()) - loss.sum()) < 1e-9 * max(1.0, loss.sum())
     np.testing.assert_allclose(ga, A.grad.numpy(), rtol=1e-10, atol=1e-12)
     np.testing.assert_allclose(gb, B.grad.numpy(), rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- k-NN graph
+def _graph_by_matrix(p, k):
+    """Independent restatement: full float64 distance matrix, per row the k
+    smallest (distance, index) over other indices, union of (min, max)."""
+    p = np.asarray(p, np.float64)
+    n = len(p)
+    d = ((p[:, None, :] - p[None, :, :]) ** 2).sum(-1)
+    edges = set()
+    for i in range(n):
+        order = sorted((d[i, j], j) for j in range(n) if j != i)
+        for _, j in order[:k]:
+            edges.add((min(i, j), max(i, j)))
+    return np.array(sorted(edges), np.int64).reshape(-1, 2)
+
+
+def test_knn_graph_hand_example():
+    p = np.array([[0, 0], [1, 0], [3, 0], [6, 0], [10, 0]], np.float32)
+    assert oracle.knn_graph(p, 1).tolist() == [[0, 1], [1, 2], [2, 3], [3, 4]]
+
+
+def test_knn_graph_line_closed_form():
+    # equally spaced line, k = 2: the path plus (0, 2) and (n-3, n-1)
+    for n in (4, 7, 30):
+        p = np.stack([np.arange(n), np.zeros(n)], 1).astype(np.float32)
+        g = oracle.knn_graph(p, 2)
+        want = sorted({(i, i + 1) for i in range(n - 1)} | {(0, 2), (n - 3, n - 1)})
+        assert g.tolist() == [list(e) for e in want]
+        assert len(g) == n + 1
+
+
+def test_knn_graph_duplicates_and_tiny():
+    p = np.zeros((3, 3), np.float32)
+    assert oracle.knn_graph(p, 1).tolist() == [[0, 1], [0, 2]]
+    assert oracle.knn_graph(p[:1], 3).shape == (0, 2)
+    assert oracle.knn_graph(p[:2], 5).tolist() == [[0, 1]]
+
+
+def test_knn_graph_matches_distance_matrix():
+    rng = np.random.default_rng(5)
+    for n, d, k in ((60, 2, 3), (80, 3, 5), (50, 5, 4)):
+        p = rng.random((n, d)).astype(np.float32)
+        assert np.array_equal(oracle.knn_graph(p, k), _graph_by_matrix(p, k))
+        q = np.round(p * 4).astype(np.float32)       # many exact ties
+        assert np.array_equal(oracle.knn_graph(q, k), _graph_by_matrix(q, k))
