@@ -309,6 +309,18 @@ def other_configs(api, torch, dev):
 
     gms = timed(graph)
     out["knn_graph_2d_10m_k10"] = {"build_and_graph_ms": gms, "edges": int(hg["e"].shape[0])}
+    # range search of every point of the same set, radius for about 10 points
+    # per query (the paper's Table 1 range search is 2D 10M; its radius is not
+    # stated)
+    tg = api.pg_tree_build(xg, 16)
+    radius = float(np.sqrt(10.0 / (np.pi * 10_000_000)))
+
+    def rng_all():
+        hg["r"] = api.pg_range(tg, None, radius)
+
+    rms = timed(rng_all)
+    out["range_2d_10m_all_r_for_10"] = {"radius": radius, "range_ms": rms, "results": int(hg["r"][0].numel())}
+    tg.free()
     del xg, hg
     # 5D / 7D clustered: 2,000,000 points, 1,000,000 separate queries, k = 16
     # (leaf size and traversal variant autotuned on the workload itself)

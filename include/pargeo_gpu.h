@@ -151,6 +151,31 @@ PG_API pg_status pg_knn_graph(const pg_tree *tree, int k, int64_t capacity, int3
                               int64_t *out_count, void *stream);
 
 /*
+ * Range search (paper Section 4: the kd-tree supports k-NN and range search;
+ * Table 1 "kd-tree Range Search").  For each query q, every point p of the
+ * tree with D(q, p) <= radius^2, D the squared Euclidean distance in float32
+ * (the same rounded chain as pg_knn) and radius^2 rounded to float32 once.
+ *   queries      device, m * dim row-major float32, or NULL for the tree's own
+ *                points (then m must equal n and row i is input row i).
+ *   radius       finite, >= 0.
+ *   capacity     int32 slots in out_idx.
+ *   out_idx      device, the concatenated result rows (tree input rows), or
+ *                NULL to compute only the offsets.  Row order: the order of
+ *                the tree walk (deterministic for a given tree and query).
+ *   out_offsets  device, m + 1 int64: query i's points are
+ *                out_idx[out_offsets[i] .. out_offsets[i+1]).
+ *   out_total    host: the number of results (written before any capacity
+ *                error, so a caller can size a second call).
+ * Stream-ordered; synchronises the stream once to read the total.  Errors:
+ * PG_EINVAL (NULL tree/out_offsets/out_total, m out of [0, 2^31), queries
+ * NULL with m != n, radius negative or not finite, more than 2^31 - 2
+ * results, or capacity below the total with out_idx given: offsets written,
+ * indices not); PG_ENOMEM for scratch (8 * m + 4 * m bytes).
+ */
+PG_API pg_status pg_range(const pg_tree *tree, const float *queries, int64_t m, float radius, int64_t capacity,
+                          int32_t *out_idx, int64_t *out_offsets, int64_t *out_total, void *stream);
+
+/*
  * Traversal variant used by pg_knn and pg_bdl_knn for every later call in this
  * process (App. A.1.3 searches each query independently; every variant returns
  * that same exact answer): 1 = one thread per query walks its own path;

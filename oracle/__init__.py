@@ -17,6 +17,8 @@ Contents
                  Erase_L, Section 5 "Parallel Batch Insertion", Appendix A.2-A.3)
                  and its live point set.
   kdtree_check   checker of the kd-tree invariants (Section 5 intro).
+  range_search   every data point within distance r of each query (Section 4:
+                 the kd-tree's range search), from the definition in float64.
   knn_graph      the k-NN graph (Section 4, geometric graph generators: the
                  k-NN graph comes from the kd-tree's k-NN search): every point
                  joined to its k nearest other points, undirected edges listed
@@ -203,4 +205,18 @@ def knn_graph(points, k: int, nthreads: int = 1) -> np.ndarray:
     if not edges:
         return np.zeros((0, 2), np.int64)
     return np.array(sorted(edges), np.int64)
+
+
+def range_search(data, queries, radius: float):
+    """For each query, the sorted indices of the data points p with
+    D(q, p) <= radius^2, in float64 on the float32 inputs (Section 4, range
+    search on the kd-tree).  Returns a list of int64 arrays."""
+    p = np.asarray(data, np.float32).astype(np.float64)
+    q = np.asarray(queries, np.float32).astype(np.float64)
+    r2 = float(np.float32(radius)) ** 2
+    out = []
+    for i in range(len(q)):
+        d = ((p - q[i]) ** 2).sum(1)
+        out.append(np.nonzero(d <= r2)[0].astype(np.int64))
+    return out
 

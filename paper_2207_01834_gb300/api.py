@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import PgError, TreeInfo, call
 
 __all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_knn", "pg_tree_free", "pg_tree_info",
-           "pg_tree_export", "pg_knn_graph", "pg_knn_set_variant", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
+           "pg_tree_export", "pg_knn_graph", "pg_range", "pg_knn_set_variant", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
            "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_knn_backward_noalloc",
            "pg_batched_chamfer",
            "pg_batched_chamfer_backward", "launch_count", "profile_enable", "profile_read", "version",
@@ -141,6 +141,26 @@ def pg_knn_graph(tree: Tree, k: int, stream=None) -> torch.Tensor:
     cnt = C.c_int64()
     call("pg_knn_graph", tree.handle, k, cap, _ptr(out), C.byref(cnt), _stream(stream))
     return out[:cnt.value]
+
+
+def pg_range(tree: Tree, queries: torch.Tensor | None, radius: float, stream=None):
+    """Points within `radius` of each query (queries=None: of each tree point).
+    Returns (idx int32 (total,), offsets int64 (m + 1,)) on the device; query
+    i's points are idx[offsets[i]:offsets[i+1]]."""
+    if queries is None:
+        m, qp = tree.n, None
+    else:
+        queries = _dev(queries, torch.float32, "queries", 2)
+        if queries.shape[1] != tree.dim:
+            raise ValueError("queries have the wrong dimension")
+        m, qp = queries.shape[0], _ptr(queries)
+    offsets = torch.empty(m + 1, dtype=torch.int64, device=tree.device)
+    total = C.c_int64()
+    call("pg_range", tree.handle, qp, m, float(radius), 0, None, _ptr(offsets), C.byref(total), _stream(stream))
+    idx = torch.empty(max(total.value, 1), dtype=torch.int32, device=tree.device)
+    call("pg_range", tree.handle, qp, m, float(radius), idx.numel(), _ptr(idx), _ptr(offsets), C.byref(total),
+         _stream(stream))
+    return idx[:total.value], offsets
 
 
 def pg_knn_set_variant(variant: int) -> None:

@@ -266,3 +266,35 @@ def test_knn_graph_matches_distance_matrix():
         assert np.array_equal(oracle.knn_graph(p, k), _graph_by_matrix(p, k))
         q = np.round(p * 4).astype(np.float32)       # many exact ties
         assert np.array_equal(oracle.knn_graph(q, k), _graph_by_matrix(q, k))
+
+
+# ---------------------------------------------------------------- range search
+def test_range_search_hand_example():
+    p = np.array([[0, 0], [1, 0], [0, 2], [3, 4]], np.float32)
+    got = oracle.range_search(p, np.array([[0, 0], [3, 3]], np.float32), 2.0)
+    assert [g.tolist() for g in got] == [[0, 1, 2], [3]]          # |(3,4)-(3,3)| = 1; (0,2) is at sqrt(10)
+
+
+def test_range_search_lattice_closed_form():
+    # radius 1 on the integer grid: the point itself and its axis neighbours
+    p = synth.lattice((7, 5))
+    got = oracle.range_search(p, p, 1.0)
+    for i, g in enumerate(got):
+        x, y = p[i]
+        want = 1 + (x > 0) + (x < 6) + (y > 0) + (y < 4)
+        assert len(g) == want
+
+
+def test_range_search_matches_cKDTree():
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(9)
+    for n, d, r in ((2000, 2, 0.03), (1500, 3, 0.1), (800, 5, 0.3)):
+        p = rng.random((n, d)).astype(np.float32)
+        q = rng.random((200, d)).astype(np.float32)
+        got = oracle.range_search(p, q, r)
+        ref = spatial.cKDTree(p.astype(np.float64)).query_ball_point(q.astype(np.float64), float(np.float32(r)))
+        for i in range(len(q)):
+            dd = ((p.astype(np.float64) - q[i].astype(np.float64)) ** 2).sum(1)
+            near = np.abs(dd - float(np.float32(r)) ** 2) <= 1e-9     # boundary cases may round either way
+            a, b = set(got[i].tolist()), set(ref[i])
+            assert {x for x in a ^ b if not near[x]} == set()
