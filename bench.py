@@ -322,6 +322,23 @@ def other_configs(api, torch, dev):
     out["range_2d_10m_all_r_for_10"] = {"radius": radius, "range_ms": rms, "results": int(hg["r"][0].numel())}
     tg.free()
     del xg, hg
+    # object-median split (the paper's other split rule) on the headline set:
+    # 10M uniform 3D points, all-kNN k = 10, leaf 48, postponed-leaf traversal
+    xo = torch.from_numpy(synth.uniform(10_000_000, 3, synth.BASE_SEED + 2)).to(dev)
+    ho = {}
+
+    def bo():
+        ho["t"] = api.pg_tree_build_split(xo, 48, api.SPLIT_OBJECT)
+
+    def qo():
+        api.pg_knn(ho["t"], None, 10)
+
+    api.pg_knn_set_variant(3)
+    obms = timed(bo)
+    oqms = timed(qo)
+    ho["t"].free()
+    out["object_median_3d_10m_k10"] = {"build_ms": obms, "knn_ms": oqms, "knn_mqps": 1e7 / oqms / 1e3}
+    del xo, ho
     # 5D / 7D clustered: 2,000,000 points, 1,000,000 separate queries, k = 16
     # (leaf size and traversal variant autotuned on the workload itself)
     from paper_2207_01834_gb300 import autotune

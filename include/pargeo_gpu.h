@@ -61,6 +61,11 @@ typedef struct pg_bdl pg_bdl;     /* one BDL-tree forest (opaque)               
 #define PG_MAX_LEAF 256
 #define PG_DEPTH_CAP 48   /* nodes deeper than this become leaves              */
 
+/* Split rules of pg_tree_build_split (paper Section 4: splits by spatial
+ * median or by object median). */
+#define PG_SPLIT_SPATIAL 0
+#define PG_SPLIT_OBJECT 1
+
 /* ------------------------------------------------------------------------
  * Static kd-tree (paper Section 5 intro; construction Appendix A.1.1).
  * ---------------------------------------------------------------------- */
@@ -77,6 +82,20 @@ typedef struct pg_bdl pg_bdl;     /* one BDL-tree forest (opaque)               
  */
 PG_API pg_status pg_tree_build(const float *points, int64_t n, int dim, int leaf_size, void *stream,
                         pg_tree **out);
+
+/*
+ * As pg_tree_build with a choice of split rule (paper Section 4: the split is
+ * by spatial median or by object median).  PG_SPLIT_SPATIAL is
+ * pg_tree_build.  PG_SPLIT_OBJECT: the split dimension is the widest extent of
+ * the node's tight box as before, and a node of c points sends its
+ * floor(c / 2) smallest points along it to the left child (ties by bucket
+ * position), so left coordinates <= split value <= right coordinates, where
+ * the split value is the first right point's coordinate; the tree is
+ * balanced.  k-NN answers do not depend on the rule.  Errors: as
+ * pg_tree_build, and PG_EINVAL for another rule.
+ */
+PG_API pg_status pg_tree_build_split(const float *points, int64_t n, int dim, int leaf_size, int split_rule,
+                                     void *stream, pg_tree **out);
 
 /*
  * Exact k-NN of m query points (device, m*dim float32) against the tree's

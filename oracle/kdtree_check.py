@@ -23,6 +23,11 @@ library, that:
   6. leaves hold at most leaf_size points unless their points are all equal or
      they sit at the depth cap.
 
+With split="object" rules 3 and 4 become the object-median split (Section 4:
+splits by spatial or by object median): the split dimension is still the
+widest extent of the tight box, the left child holds floor(c/2) of the node's
+c points, and left coordinates <= value <= right coordinates along it.
+
 The exported layout (see the C header) is: per node, float32 words
 lo0[DC], hi0[DC], lo1[DC], hi1[DC] followed by int32 words ref0, cnt0, ref1,
 cnt1 (cnt > 0: leaf child holding buckets [ref, ref+cnt); cnt == 0: internal
@@ -41,7 +46,7 @@ def _fail(msg):
     raise TreeInvariantError(msg)
 
 
-def check_tree(points, exp, leaf_size: int, depth_cap: int) -> dict:
+def check_tree(points, exp, leaf_size: int, depth_cap: int, split: str = "spatial") -> dict:
     """Check an exported tree against its input points.
 
     points : (n, dim) float32 input
@@ -142,8 +147,6 @@ def check_tree(points, exp, leaf_size: int, depth_cap: int) -> dict:
         sv = np.float32(exp["split_val"][node])
         if not (0 <= sd < dim):
             _fail(f"node {node}: split dim {sd}")
-        if not np.all(coords[l0:l1, sd] < sv) or not np.all(coords[r0:r1, sd] >= sv):
-            _fail(f"node {node}: split property violated (dim {sd}, value {sv})")
         seg = coords[l0:r1]
         tlo = seg.min(axis=0)
         thi = seg.max(axis=0)
@@ -151,6 +154,16 @@ def check_tree(points, exp, leaf_size: int, depth_cap: int) -> dict:
         want_dim = int(np.argmax(ext))
         if ext[want_dim] <= 0:
             _fail(f"node {node}: split of a set of identical points")
+        if split == "object":
+            if sd != want_dim:
+                _fail(f"node {node}: split dim {sd} is not the widest {want_dim}")
+            if l1 - l0 != (r1 - l0) // 2:
+                _fail(f"node {node}: left child holds {l1 - l0} of {r1 - l0} points, not the lower half")
+            if not np.all(coords[l0:l1, sd] <= sv) or not np.all(coords[r0:r1, sd] >= sv):
+                _fail(f"node {node}: object-median split property violated (dim {sd}, value {sv})")
+            continue
+        if not np.all(coords[l0:l1, sd] < sv) or not np.all(coords[r0:r1, sd] >= sv):
+            _fail(f"node {node}: split property violated (dim {sd}, value {sv})")
         lo_s, hi_s = tlo[want_dim], thi[want_dim]
         mid = np.float32(np.float32(0.5) * lo_s) + np.float32(np.float32(0.5) * hi_s)
         mid = np.float32(mid)

@@ -41,6 +41,7 @@ _S = C.c_int  # pg_status
 
 SIGNATURES = {
     "pg_tree_build": (_S, [_P, _I64, _I, _I, _P, C.POINTER(_P)]),
+    "pg_tree_build_split": (_S, [_P, _I64, _I, _I, _I, _P, C.POINTER(_P)]),
     "pg_knn": (_S, [_P, _P, _I64, _I, _P, _P, _P]),
     "pg_tree_free": (_S, [_P]),
     "pg_tree_info": (_S, [_P, C.POINTER(TreeInfo)]),

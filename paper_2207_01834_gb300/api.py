@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import PgError, TreeInfo, call
 
-__all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_knn", "pg_tree_free", "pg_tree_info",
+__all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_tree_build_split", "pg_knn", "pg_tree_free", "pg_tree_info",
            "pg_tree_export", "pg_knn_graph", "pg_range", "pg_knn_set_variant", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
            "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_knn_backward_noalloc",
            "pg_batched_chamfer",
@@ -83,6 +83,20 @@ def pg_tree_build(points: torch.Tensor, leaf_size: int = 16, stream=None) -> Tre
     n, dim = pts.shape
     out = C.c_void_p()
     call("pg_tree_build", _ptr(pts) if n else None, n, dim, leaf_size, _stream(stream), C.byref(out))
+    return Tree(out.value, (n, dim), pts.device)
+
+
+SPLIT_SPATIAL, SPLIT_OBJECT = 0, 1
+
+
+def pg_tree_build_split(points: torch.Tensor, leaf_size: int = 16, split_rule: int = SPLIT_SPATIAL,
+                        stream=None) -> Tree:
+    """kd-tree with the spatial-median (0) or object-median (1) split."""
+    pts = _dev(points, torch.float32, "points", 2)
+    n, dim = pts.shape
+    out = C.c_void_p()
+    call("pg_tree_build_split", _ptr(pts) if n else None, n, dim, leaf_size, split_rule, _stream(stream),
+         C.byref(out))
     return Tree(out.value, (n, dim), pts.device)
 
 

@@ -5,7 +5,7 @@
 #include "internal.h"
 
 namespace pg {
-pg_status build_rows(const float *pts, int64_t n, int dim, int leaf, cudaStream_t s, pg_tree *t);
+pg_status build_rows(const float *pts, int64_t n, int dim, int leaf, int rule, cudaStream_t s, pg_tree *t);
 }
 
 using namespace pg;
@@ -18,7 +18,14 @@ static pg_status check_dim(int dim) {
 extern "C" {
 
 pg_status pg_tree_build(const float *points, int64_t n, int dim, int leaf_size, void *stream, pg_tree **out) {
+    return pg_tree_build_split(points, n, dim, leaf_size, PG_SPLIT_SPATIAL, stream, out);
+}
+
+pg_status pg_tree_build_split(const float *points, int64_t n, int dim, int leaf_size, int split_rule, void *stream,
+                              pg_tree **out) {
     if (!out) return fail(PG_EINVAL, "pg_tree_build: out is NULL");
+    if (split_rule != PG_SPLIT_SPATIAL && split_rule != PG_SPLIT_OBJECT)
+        return fail(PG_EINVAL, "pg_tree_build_split: unknown split rule");
     *out = nullptr;
     PG_TRY(check_dim(dim));
     if (n < 0 || n >= (int64_t)1 << 31) return fail(PG_EINVAL, "pg_tree_build: n must be in [0, 2^31)");
@@ -27,7 +34,7 @@ pg_status pg_tree_build(const float *points, int64_t n, int dim, int leaf_size, 
     pg_tree *t = new (std::nothrow) pg_tree();
     if (!t) return fail(PG_ENOMEM, "pg_tree_build: host allocation");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    pg_status st = build_rows(points, n, dim, leaf_size, s, t);
+    pg_status st = build_rows(points, n, dim, leaf_size, split_rule, s, t);
     if (st != PG_OK) {
         tree_release(t);
         delete t;

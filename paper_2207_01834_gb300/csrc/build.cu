@@ -115,10 +115,13 @@ __device__ __forceinline__ unsigned seg_combine(unsigned a, unsigned b) {   // a
 
 // Flags and segment starts of one tile; every warp-row's segmented count
 // goes to rowsum[row * PT_WARPS + warp].
-template <int DC>
+// PRE: the "goes left" flag of each position is given in pflag (object-median
+// levels) instead of computed from the split value.
+template <int DC, bool PRE = false>
 __device__ __forceinline__ void tile_flags(int n, int base, const float *pf, const int *seg_of,
                                            const int *split_flag, const int *sdim, const float *sval,
-                                           unsigned &fbits, unsigned &rbits, unsigned *rowsum) {
+                                           unsigned &fbits, unsigned &rbits, unsigned *rowsum,
+                                           const int *pflag = nullptr) {
     constexpr int W = bucket_w(DC);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     fbits = 0;
@@ -132,7 +135,7 @@ __device__ __forceinline__ void tile_flags(int n, int base, const float *pf, con
         if (lane == 0) sp = (valid && i > 0) ? seg_of[i - 1] : -2;
         const bool start = valid && s != sp;
         int f = 0;
-        if (valid && s >= 0 && split_flag[s]) f = pf[(size_t)i * 4 * W + sdim[s]] < sval[s];
+        if (valid && s >= 0 && split_flag[s]) f = PRE ? pflag[i] : pf[(size_t)i * 4 * W + sdim[s]] < sval[s];
         fbits |= (unsigned)f << j;
         rbits |= (unsigned)start << j;
         const unsigned F = __ballot_sync(0xffffffffu, f), R = __ballot_sync(0xffffffffu, start);
@@ -143,18 +146,19 @@ __device__ __forceinline__ void tile_flags(int n, int base, const float *pf, con
     }
 }
 
-template <int DC>
+template <int DC, bool PRE = false>
 __global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const float4 *__restrict__ P,
                                                            const int *__restrict__ seg_of,
                                                            const int *__restrict__ split_flag,
                                                            const int *__restrict__ sdim,
                                                            const float *__restrict__ sval,
-                                                           const int *__restrict__ T, unsigned *__restrict__ tsum) {
+                                                           const int *__restrict__ T, unsigned *__restrict__ tsum,
+                                                           const int *__restrict__ pflag = nullptr) {
     if (*T == 0) return;
     __shared__ unsigned rowsum[PT_ROWS * PT_WARPS];
     unsigned fbits, rbits;
-    tile_flags<DC>((int)n, blockIdx.x * PT_TILE, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval,
-                   fbits, rbits, rowsum);
+    tile_flags<DC, PRE>((int)n, blockIdx.x * PT_TILE, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval,
+                   fbits, rbits, rowsum, pflag);
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned a = 0;
@@ -476,7 +480,7 @@ pg_status level_segments(int S_max, int *ctl, const Segs &cur, const Segs &nxt, 
 // and reduce the children's tight boxes: per tile in shared memory (children
 // of a tile are few and consecutive), then one global atomic per child and
 // dimension; a child that finds its slot taken goes straight to global memory.
-template <int DC>
+template <int DC, bool PRE = false>
 __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
                                                      const int *__restrict__ seg_of, int *__restrict__ seg_of_nx,
                                                      const int *__restrict__ start, const int *__restrict__ end,
@@ -485,7 +489,8 @@ __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n,
                                                      const int *__restrict__ sdim, const float *__restrict__ sval,
                                                      const unsigned *__restrict__ tcarry, int *__restrict__ nx_start,
                                                      int *__restrict__ nx_end, int *__restrict__ nx_lo,
-                                                     int *__restrict__ nx_hi, const int *__restrict__ T) {
+                                                     int *__restrict__ nx_hi, const int *__restrict__ T,
+                                                     const int *__restrict__ pflag = nullptr) {
     constexpr int W = bucket_w(DC);
     if (*T == 0) return;
     __shared__ unsigned rowsum[PT_ROWS * PT_WARPS];
@@ -500,8 +505,8 @@ __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n,
         b_hi[x] = (int)0x807fffffu;
     }
     unsigned fbits, rbits;
-    tile_flags<DC>(n32, base, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval, fbits, rbits,
-                   rowsum);
+    tile_flags<DC, PRE>(n32, base, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval, fbits, rbits,
+                   rowsum, pflag);
     __syncthreads();
     // segmented exclusive scan of the tile's warp-rows (warp 0, 4 per lane)
     if (warp == 0) {
@@ -601,6 +606,65 @@ __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n,
     }
 }
 
+// ---------------------------------------------------------------- object median
+// Object-median levels (paper Section 4: kd-tree splits by spatial median or
+// by object median): a split segment of c points sends its floor(c / 2)
+// smallest points along the split dimension to the left child, ties by
+// position.  The points of all split segments are put in (segment,
+// coordinate, position) order by two stable radix sorts (coordinate first,
+// then segment); a point's rank inside its segment's run decides its side,
+// and the point of rank floor(c / 2) gives the node's split value.
+
+// Once the loop is done (T == 0) the segment ids of later levels were never
+// written, so they are not read: every key becomes the sentinel.
+template <int DC>
+__global__ void k_obj_keys(int n, const float4 *__restrict__ P, const int *__restrict__ seg_of,
+                           const int *__restrict__ split_flag, const int *__restrict__ sdim,
+                           const int *__restrict__ T, uint32_t sentinel, uint32_t *__restrict__ kc,
+                           uint32_t *__restrict__ ks, uint32_t *__restrict__ val) {
+    constexpr int W = bucket_w(DC);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = *T != 0 ? seg_of[i] : -1;
+    const bool a = s >= 0 && split_flag[s];
+    const float x = a ? reinterpret_cast<const float *>(P)[(size_t)i * 4 * W + sdim[s]] : 0.f;
+    kc[i] = a ? ((uint32_t)f2o(x) ^ 0x80000000u) : 0xffffffffu;   // unsigned key in float order
+    ks[i] = a ? (uint32_t)s : sentinel;
+    val[i] = (uint32_t)i;
+}
+
+__global__ void k_obj_gather(int n, const uint32_t *__restrict__ ks, const uint32_t *__restrict__ pos,
+                             uint32_t *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = ks[pos[j]];
+}
+
+__global__ void k_obj_first(int n, const uint32_t *__restrict__ sk, uint32_t sentinel, int *__restrict__ first) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t s = sk[j];
+    if (s != sentinel && (j == 0 || sk[j - 1] != s)) first[s] = j;
+}
+
+template <int DC>
+__global__ void k_obj_flags(int n, const uint32_t *__restrict__ sk, const uint32_t *__restrict__ spos,
+                            uint32_t sentinel, const int *__restrict__ first, const int *__restrict__ start,
+                            const int *__restrict__ end, const int *__restrict__ split_rank,
+                            const int *__restrict__ sdim, const float4 *__restrict__ P, const int *__restrict__ ctl,
+                            int *__restrict__ pflag, float *__restrict__ n_sval) {
+    constexpr int W = bucket_w(DC);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t s = sk[j];
+    if (s == sentinel) return;
+    const int rank = j - first[s];
+    const int half = (end[s] - start[s]) / 2;
+    const int i = (int)spos[j];
+    pflag[i] = rank < half;
+    if (rank == half)   // the first right point: the node's split value
+        n_sval[ctl[CTL_NB] + split_rank[s]] = reinterpret_cast<const float *>(P)[(size_t)i * 4 * W + sdim[s]];
+}
+
 constexpr int FIN_NT = 512;                  // threads of a finisher block
 constexpr size_t kFinSmemBudget = 110 * 1024;   // shared memory of a finisher block (two blocks per SM)
 
@@ -652,7 +716,7 @@ __global__ void k_leaf_parents(const float4 *__restrict__ nodes, int num_nodes, 
 
 template <int DC>
 struct Builder {
-    static pg_status run(float4 *packed, int *box, int64_t n, int leaf, cudaStream_t s, pg_tree *t);
+    static pg_status run(float4 *packed, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t);
 };
 
 pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
@@ -694,7 +758,7 @@ pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
 }
 
 template <int DC>
-pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream_t s, pg_tree *t) {
+pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t) {
     constexpr int W = bucket_w(DC);
     // Split segments hold more than `leaf` points and are disjoint, so a level
     // has at most 2*floor(n/(leaf+1)) segments.
@@ -744,14 +808,15 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     if (!t->leaf_parent) PG_TRY(dalloc_n(&t->leaf_parent, (size_t)n, s));
     PG_CUDA(cudaMemsetAsync(t->leaf_parent, 0xff, sizeof(int) * (size_t)n, s));   // a leaf root keeps -1
     // Segments of up to fin_max points are finished in one block's shared memory.
-    const int fin_max = smem_build_points(DC, leaf, kFinSmemBudget);
+    // (object-median trees split every level on the device: no finisher)
+    const int fin_max = rule == PG_SPLIT_OBJECT ? 0 : smem_build_points(DC, leaf, kFinSmemBudget);
     const int fin_sc = smem_seg_cap(fin_max, leaf);
     const size_t fin_smem = smem_build_bytes(fin_max, fin_sc, DC);
     // Node slots: every global split holds more than fin_max points (at most
     // n/(fin_max+1) per level), and finisher segment [st, en) reserves slots
     // [nb + st, nb + en) after the nb global nodes.  Unused slots stay
     // all-ones (cnt = -1).
-    const int64_t slots = (int64_t)(PG_DEPTH_CAP + 1) * (n / (fin_max + 1)) + 64 + n;
+    const int64_t slots = rule == PG_SPLIT_OBJECT ? n + 64 : (int64_t)(PG_DEPTH_CAP + 1) * (n / (fin_max + 1)) + 64 + n;
     if (slots >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "tree build: too many node slots");
     PG_TRY(grow_nodes(t, (int)slots, s));
     PG_CUDA(cudaMemsetAsync(t->nodes, 0xff, sizeof(float4) * node_w(DC) * (size_t)slots, s));
@@ -772,7 +837,19 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
     // The host enqueues levels without waiting; it starts checking for the
     // end around the level where uniform data would stop.
     int est = 1;
-    while (((int64_t)fin_max << (est - 1)) < n && est < PG_DEPTH_CAP) ++est;
+    const int64_t unit = rule == PG_SPLIT_OBJECT ? (int64_t)leaf + 1 : fin_max;
+    while ((unit << (est - 1)) < n && est < PG_DEPTH_CAP) ++est;
+    // object-median scratch: keys, segment keys, positions, two temporaries, a
+    // gathered copy, flags (n each) and the first sorted index of each segment
+    Scratch sObj;
+    uint32_t *okc = nullptr, *oks = nullptr, *ov = nullptr, *ot0 = nullptr, *ot1 = nullptr, *oks2 = nullptr;
+    int *opflag = nullptr, *ofirst = nullptr;
+    if (rule == PG_SPLIT_OBJECT) {
+        PG_TRY(sObj.alloc(sizeof(uint32_t) * (size_t)(7 * n + seg_cap + 8), s));
+        okc = sObj.as<uint32_t>(); oks = okc + n; ov = oks + n; ot0 = ov + n; ot1 = ot0 + n; oks2 = ot1 + n;
+        opflag = reinterpret_cast<int *>(oks2 + n);
+        ofirst = opflag + n;
+    }
     int hctl[CTL_WORDS] = {0};
     int level = 0;
     for (; level <= PG_DEPTH_CAP + 1; ++level) {
@@ -781,11 +858,38 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, cudaStream
                                   fin_rank, fin, t->nodes, t->split_dim, t->split_val, t->node_range, t->parent,
                                   nullptr, 0, nullptr, s));
         const int *T = split_rank + S_max;
-        k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<unsigned>());
-        k_part_carry<<<1, 1024, 0, s>>>(sBsum.as<unsigned>(), ntiles, T, ctl, fin_rank + S_max, level);
-        count_launch();
-        count_launch();
-        {
+        if (rule == PG_SPLIT_OBJECT) {
+            const int g = ceil_div_i(n, BT);
+            const uint32_t sentinel = (uint32_t)S_max;
+            int sbits = 1;
+            while (sbits < 32 && ((int64_t)1 << sbits) <= (int64_t)S_max) ++sbits;
+            k_obj_keys<DC><<<g, BT, 0, s>>>((int)n, P, seg_of, split_flag, sdim, T, sentinel, okc, oks, ov);
+            count_launch();
+            uint32_t *k1 = nullptr, *v1 = nullptr, *k2 = nullptr, *v2 = nullptr;
+            PG_TRY(radix_sort_pairs(okc, ov, false, ot0, ot1, n, 32, s, &k1, &v1));
+            k_obj_gather<<<g, BT, 0, s>>>((int)n, oks, v1, oks2);
+            count_launch();
+            // temporaries for the second sort: two buffers other than oks2 and v1
+            uint32_t *cand[4] = {okc, ov, ot0, ot1}, *tmp[2];
+            int nt = 0;
+            for (uint32_t *c : cand)
+                if (c != v1 && nt < 2) tmp[nt++] = c;
+            PG_TRY(radix_sort_pairs(oks2, v1, false, tmp[0], tmp[1], n, sbits, s, &k2, &v2));
+            k_obj_first<<<g, BT, 0, s>>>((int)n, k2, sentinel, ofirst);
+            k_obj_flags<DC><<<g, BT, 0, s>>>((int)n, k2, v2, sentinel, ofirst, cur.start, cur.end, split_rank, sdim, P,
+                                            ctl, opflag, t->split_val);
+            k_part_tiles<DC, true><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T,
+                                                                 sBsum.as<unsigned>(), opflag);
+            k_part_carry<<<1, 1024, 0, s>>>(sBsum.as<unsigned>(), ntiles, T, ctl, fin_rank + S_max, level);
+            k_part<DC, true><<<ntiles, PT_THREADS, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
+                                                           split_rank, sdim, sval, sBsum.as<unsigned>(), nxt.start,
+                                                           nxt.end, nxt.lo, nxt.hi, T, opflag);
+            for (int c = 0; c < 5; ++c) count_launch();
+        } else {
+            k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<unsigned>());
+            k_part_carry<<<1, 1024, 0, s>>>(sBsum.as<unsigned>(), ntiles, T, ctl, fin_rank + S_max, level);
+            count_launch();
+            count_launch();
             KTimer kt("build_scatter", s);
             k_part<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
                                                      split_rank, sdim, sval, sBsum.as<unsigned>(), nxt.start, nxt.end,
@@ -991,7 +1095,7 @@ pg_status forest_levels(int dc, const ForestArgs &fa, cudaStream_t s) {
 
 // Packs and builds in one go (the packed array is allocated here).
 static pg_status build_from(const float *src, const int32_t *rows, const int32_t *ids, int64_t n, int dim,
-                            int leaf, cudaStream_t s, pg_tree *t) {
+                            int leaf, int rule, cudaStream_t s, pg_tree *t) {
     const int dc = dim_class(dim);
     t->n = n;
     t->dim = dim;
@@ -1034,7 +1138,7 @@ static pg_status build_from(const float *src, const int32_t *rows, const int32_t
             return fail(PG_EINVAL, "points must have finite coordinates");
         }
     }
-    PG_DC_SWITCH(dc, st = Builder<DCV>::run(packed, box.as<int>(), n, leaf, s, t));
+    PG_DC_SWITCH(dc, st = Builder<DCV>::run(packed, box.as<int>(), n, leaf, rule, s, t));
     if (st != PG_OK) {
         if (t->bucket != packed) dfree(packed, s);
         return st;
@@ -1042,13 +1146,13 @@ static pg_status build_from(const float *src, const int32_t *rows, const int32_t
     return tree_upload_desc(t);
 }
 
-pg_status build_rows(const float *pts, int64_t n, int dim, int leaf, cudaStream_t s, pg_tree *t) {
-    return build_from(pts, nullptr, nullptr, n, dim, leaf, s, t);
+pg_status build_rows(const float *pts, int64_t n, int dim, int leaf, int rule, cudaStream_t s, pg_tree *t) {
+    return build_from(pts, nullptr, nullptr, n, dim, leaf, rule, s, t);
 }
 
 pg_status build_gather(const float *store, const int32_t *ids, int64_t n, int dim, int leaf, cudaStream_t s,
                        pg_tree *t) {
-    return build_from(store, ids, ids, n, dim, leaf, s, t);
+    return build_from(store, ids, ids, n, dim, leaf, PG_SPLIT_SPATIAL, s, t);
 }
 
 TreeDesc tree_desc(const pg_tree *t) {

@@ -74,6 +74,42 @@ def test_tree_invariants(api, case):
     tree.free()
 
 
+OBJECT_CASES = ["uniform2d", "uniform3d_leaf8", "gmm5d_leaf32", "gmm7d", "dim1", "dim16", "all_equal",
+                "collinear", "one_point", "below_leaf", "duplicates", "lattice3d", "depth_cap_chain", "leaf1"]
+
+
+@pytest.mark.parametrize("case", OBJECT_CASES)
+def test_object_median_tree_invariants(api, case):
+    make, leaf = TREE_CASES[case]
+    pts = make()
+    tree = api.pg_tree_build_split(_cuda(pts), leaf_size=leaf, split_rule=api.SPLIT_OBJECT)
+    exp = tree.export()
+    st = check_tree(pts, exp, leaf_size=leaf, depth_cap=48, split="object")
+    assert exp["depth"] == st["depth"]
+    if len(pts) > 1 and case not in ("all_equal",):
+        # balanced: depth at most ceil(log2(n / leaf)) + 1
+        assert st["depth"] <= int(np.ceil(np.log2(max(len(pts) / leaf, 1)))) + 1
+    tree.free()
+
+
+@pytest.mark.parametrize("v", [1, 2, 3])
+def test_object_median_knn_equals_spatial(api, v):
+    """k-NN answers do not depend on the split rule: bit-identical outputs."""
+    pts = synth.gmm(60000, 3, 44)
+    q = synth.gmm(8000, 3, 45)
+    ts = api.pg_tree_build(_cuda(pts), leaf_size=16)
+    to = api.pg_tree_build_split(_cuda(pts), leaf_size=16, split_rule=api.SPLIT_OBJECT)
+    api.pg_knn_set_variant(v)
+    try:
+        for a, b in zip(api.pg_knn(ts, _cuda(q), 9) + api.pg_knn(ts, None, 6),
+                        api.pg_knn(to, _cuda(q), 9) + api.pg_knn(to, None, 6)):
+            assert torch.equal(a, b)
+    finally:
+        api.pg_knn_set_variant(0)
+    ts.free()
+    to.free()
+
+
 def test_empty_tree(api):
     tree = api.pg_tree_build(torch.zeros((0, 3), device="cuda"), leaf_size=16)
     q = _cuda(synth.uniform(10, 3, 1))

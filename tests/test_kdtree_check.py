@@ -73,3 +73,40 @@ def test_leaf_size_enforced():
     pts, exp = _hand_tree()
     with pytest.raises(TreeInvariantError):
         check_tree(pts, exp, leaf_size=1, depth_cap=10)
+
+
+def _one_split_tree(pts, left, right, sd, sv):
+    """A root node splitting `pts` into two leaves (left ids, right ids) with tight boxes."""
+    dc = pts.shape[1]
+    order = list(left) + list(right)
+    bucket = np.zeros((len(pts), 4), np.float32)
+    bucket[:, :dc] = pts[order]
+    bucket[:, dc] = np.asarray(order, np.int32).view(np.float32)
+    node = np.zeros((1, 4 * dc + 4), np.float32)
+    for c, ids in enumerate((left, right)):
+        node[0, 2 * c * dc:2 * c * dc + dc] = pts[list(ids)].min(0)
+        node[0, 2 * c * dc + dc:2 * c * dc + 2 * dc] = pts[list(ids)].max(0)
+    node[0, 4 * dc:4 * dc + 4] = np.asarray([0, len(left), len(left), len(right)], np.int32).view(np.float32)
+    return {"dim": dc, "dc": dc, "nodes": node, "split_dim": np.array([sd], np.int32),
+            "split_val": np.array([sv], np.float32), "bucket": bucket, "root_ref": 0, "root_cnt": 0,
+            "root_lo": pts.min(0), "root_hi": pts.max(0), "num_nodes": 1}
+
+
+def test_object_median_rule():
+    pts = np.array([[0, 0], [3, 1], [1, 2], [2, 0]], np.float32)
+    good = _one_split_tree(pts, [0, 2], [3, 1], 0, 2.0)        # the two smallest x left, value = first right x
+    check_tree(pts, good, leaf_size=2, depth_cap=10, split="object")
+    with pytest.raises(TreeInvariantError):
+        check_tree(pts, good, leaf_size=2, depth_cap=10)       # not the spatial median (1.5)
+    bad_sizes = _one_split_tree(pts, [0], [2, 3, 1], 0, 1.0)   # left is not the lower half
+    with pytest.raises(TreeInvariantError):
+        check_tree(pts, bad_sizes, leaf_size=3, depth_cap=10, split="object")
+    bad_value = _one_split_tree(pts, [0, 2], [3, 1], 0, 0.5)   # a left point lies above the value
+    with pytest.raises(TreeInvariantError):
+        check_tree(pts, bad_value, leaf_size=2, depth_cap=10, split="object")
+    bad_dim = _one_split_tree(pts, [0, 3], [1, 2], 1, 1.0)     # y is not the widest extent
+    with pytest.raises(TreeInvariantError):
+        check_tree(pts, bad_dim, leaf_size=2, depth_cap=10, split="object")
+    ties = np.array([[0, 0], [1, 0], [1, 1], [1, 2], [2, 0]], np.float32)
+    tied = _one_split_tree(ties, [0, 1], [2, 3, 4], 0, 1.0)    # equal coordinates on both sides are allowed
+    check_tree(ties, tied, leaf_size=3, depth_cap=10, split="object")
