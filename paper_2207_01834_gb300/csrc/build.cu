@@ -714,6 +714,26 @@ __global__ void k_leaf_parents(const float4 *__restrict__ nodes, int num_nodes, 
     }
 }
 
+// Level 0 of a single tree: one segment over all n points with the packed
+// root box; the control block starts with one live segment.
+template <int DC>
+__global__ void k_level0_init(int n, const int *__restrict__ box, Segs cur, int *__restrict__ ctl) {
+    const int t = threadIdx.x;
+    if (t == 0) {
+        cur.start[0] = 0;
+        cur.end[0] = n;
+        cur.parent[0] = -1;
+        cur.side[0] = 0;
+        cur.depth[0] = 0;
+        for (int w = 0; w < CTL_WORDS; ++w) ctl[w] = 0;
+        ctl[CTL_S] = 1;
+    }
+    if (t < DC) {
+        cur.lo[t] = box[t];
+        cur.hi[t] = box[DC + t];
+    }
+}
+
 template <int DC>
 struct Builder {
     static pg_status run(float4 *packed, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t);
@@ -804,9 +824,9 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
 
     float4 *P = P0, *Q = sP1.as<float4>();
     int *seg_of = sSeg0.as<int>(), *seg_of_nx = sSeg1.as<int>();
-    PG_CUDA(cudaMemsetAsync(seg_of, 0, sizeof(int) * (size_t)n, s));   // all in segment 0
+    PG_TRY(fill_words(seg_of, 0u, (size_t)n, s));   // all in segment 0
     if (!t->leaf_parent) PG_TRY(dalloc_n(&t->leaf_parent, (size_t)n, s));
-    PG_CUDA(cudaMemsetAsync(t->leaf_parent, 0xff, sizeof(int) * (size_t)n, s));   // a leaf root keeps -1
+    PG_TRY(fill_words(t->leaf_parent, 0xffffffffu, (size_t)n, s));   // a leaf root keeps -1
     // Segments of up to fin_max points are finished in one block's shared memory.
     // (object-median trees split every level on the device: no finisher)
     const int fin_max = rule == PG_SPLIT_OBJECT ? 0 : smem_build_points(DC, leaf, kFinSmemBudget);
@@ -819,20 +839,12 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
     const int64_t slots = rule == PG_SPLIT_OBJECT ? n + 64 : (int64_t)(PG_DEPTH_CAP + 1) * (n / (fin_max + 1)) + 64 + n;
     if (slots >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "tree build: too many node slots");
     PG_TRY(grow_nodes(t, (int)slots, s));
-    PG_CUDA(cudaMemsetAsync(t->nodes, 0xff, sizeof(float4) * node_w(DC) * (size_t)slots, s));
+    PG_TRY(fill_words(t->nodes, 0xffffffffu, 4 * node_w(DC) * (size_t)slots, s));
 
     // level 0: one segment covering everything, box reduced by k_pack
     {
-        int h[5] = {0, (int)n, -1, 0, 0};
-        PG_CUDA(cudaMemcpyAsync(cur.start, &h[0], sizeof(int), cudaMemcpyHostToDevice, s));
-        PG_CUDA(cudaMemcpyAsync(cur.end, &h[1], sizeof(int), cudaMemcpyHostToDevice, s));
-        PG_CUDA(cudaMemcpyAsync(cur.parent, &h[2], sizeof(int), cudaMemcpyHostToDevice, s));
-        PG_CUDA(cudaMemcpyAsync(cur.side, &h[3], sizeof(int), cudaMemcpyHostToDevice, s));
-        PG_CUDA(cudaMemcpyAsync(cur.depth, &h[4], sizeof(int), cudaMemcpyHostToDevice, s));
-        PG_CUDA(cudaMemcpyAsync(cur.lo, box, sizeof(int) * DC, cudaMemcpyDeviceToDevice, s));
-        PG_CUDA(cudaMemcpyAsync(cur.hi, box + DC, sizeof(int) * DC, cudaMemcpyDeviceToDevice, s));
-        int c[CTL_WORDS] = {1, 0, 0, 0, 0, 0, 0};
-        PG_CUDA(cudaMemcpyAsync(ctl, c, sizeof(c), cudaMemcpyHostToDevice, s));
+        k_level0_init<DC><<<1, 32, 0, s>>>((int)n, box, cur, ctl);
+        count_launch();
     }
     // The host enqueues levels without waiting; it starts checking for the
     // end around the level where uniform data would stop.
@@ -919,7 +931,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
         Scratch sRec;
         PG_TRY(sRec.alloc(sizeof(int) * 3, s));
         int *rec = sRec.as<int>();
-        PG_CUDA(cudaMemsetAsync(rec, 0, sizeof(int) * 3, s));
+        PG_TRY(fill_words(rec, 0u, 3, s));
         {
             KTimer kt("build_finish", s);
             k_finish<DC><<<fin_total, FIN_NT, fin_smem, s>>>(fin, P, leaf, fin_max, fin_sc, ctl, t->nodes,
@@ -1171,7 +1183,8 @@ TreeDesc tree_desc(const pg_tree *t) {
 pg_status tree_upload_desc(pg_tree *t) {
     if (!t->desc) PG_TRY(dalloc_n(&t->desc, 1, t->stream));
     TreeDesc d = tree_desc(t);
-    PG_CUDA(cudaMemcpyAsync(t->desc, &d, sizeof(d), cudaMemcpyHostToDevice, t->stream));
+    static_assert(sizeof(TreeDesc) <= kStoreSmallBytes && sizeof(TreeDesc) % 4 == 0, "descriptor size");
+    PG_TRY(store_small(t->desc, &d, sizeof(d), t->stream));
     PG_CUDA(cudaStreamSynchronize(t->stream));
     return PG_OK;
 }

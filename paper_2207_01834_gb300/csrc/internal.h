@@ -32,6 +32,14 @@ struct pg_tree {
 
 namespace pg {
 
+// ---- runtime.cu
+// Fill `words` 32-bit words with `value`, and store up to kStoreSmallBytes of
+// host data into device memory, by kernels (stream-ordered; no copy engine, so
+// neither waits behind a caller's bulk copy in flight).
+constexpr size_t kStoreSmallBytes = 256;
+pg_status fill_words(void *dst, uint32_t value, size_t words, cudaStream_t s);
+pg_status store_small(void *dev_dst, const void *host_src, size_t bytes, cudaStream_t s);
+
 // ---- scan.cu
 // out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total.
 pg_status exclusive_scan(const int *in, int *out, int64_t n, cudaStream_t s);

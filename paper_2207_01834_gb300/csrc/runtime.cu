@@ -1,5 +1,6 @@
 // Runtime services of the library: error state, device memory, launch
 // counting and the kernel timer used for roofline measurements.
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -8,6 +9,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "internal.h"
 
 namespace pg {
 
@@ -78,6 +80,48 @@ __global__ void k_read_small(const int *__restrict__ src, int *dst, int words) {
 constexpr size_t kReadSmallBytes = 1024;
 thread_local std::map<int, int *> t_mapped;   // device -> mapped buffer (kept for the thread's life)
 }  // namespace
+
+// Fills and small uploads by kernels, for the same reason: neither waits
+// behind a bulk copy in flight on a copy engine.
+namespace {
+__global__ void k_fill_words(uint32_t *__restrict__ p, uint32_t v, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        uint4 *q = reinterpret_cast<uint4 *>(p);
+        const uint4 vv = make_uint4(v, v, v, v);
+        for (size_t j = i; j < n / 4; j += stride) q[j] = vv;
+        for (size_t j = n / 4 * 4 + i; j < n; j += stride) p[j] = v;
+    } else {
+        for (size_t j = i; j < n; j += stride) p[j] = v;
+    }
+}
+struct SmallBlob {
+    uint32_t w[kStoreSmallBytes / 4];
+};
+__global__ void k_store_words(uint32_t *__restrict__ dst, SmallBlob b, int words) {
+    const int i = threadIdx.x;
+    if (i < words) dst[i] = b.w[i];
+}
+}  // namespace
+
+pg_status fill_words(void *dst, uint32_t value, size_t words, cudaStream_t s) {
+    if (words == 0) return PG_OK;
+    const int grid = (int)std::min<size_t>((words / 4 + 255) / 256 + 1, (size_t)num_sms() * 8);
+    k_fill_words<<<grid, 256, 0, s>>>(static_cast<uint32_t *>(dst), value, words);
+    count_launch();
+    return check_launch("fill_words");
+}
+
+pg_status store_small(void *dev_dst, const void *host_src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return PG_OK;
+    if (bytes > kStoreSmallBytes || bytes % 4) return fail(PG_EINVAL, "store_small: at most 256 bytes, whole words");
+    SmallBlob b;
+    memcpy(b.w, host_src, bytes);
+    k_store_words<<<1, (int)(kStoreSmallBytes / 4), 0, s>>>(static_cast<uint32_t *>(dev_dst), b, (int)(bytes / 4));
+    count_launch();
+    return check_launch("store_small");
+}
 
 pg_status read_small(void *host_dst, const void *dev_src, size_t bytes, cudaStream_t s) {
     if (bytes == 0) return PG_OK;
