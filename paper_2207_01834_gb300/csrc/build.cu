@@ -120,12 +120,10 @@ __device__ __forceinline__ unsigned seg_combine(unsigned a, unsigned b) {   // a
 template <int DC, bool PRE = false>
 __device__ __forceinline__ void tile_flags(int n, int base, const float *pf, const int *seg_of,
                                            const int *split_flag, const int *sdim, const float *sval,
-                                           unsigned &fbits, unsigned &rbits, unsigned *rowsum,
+                                           unsigned *fword, unsigned *rword, unsigned *rowsum,
                                            const int *pflag = nullptr) {
     constexpr int W = bucket_w(DC);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    fbits = 0;
-    rbits = 0;
 #pragma unroll
     for (int j = 0; j < PT_ROWS; ++j) {
         const int i = base + j * PT_THREADS + threadIdx.x;
@@ -136,15 +134,22 @@ __device__ __forceinline__ void tile_flags(int n, int base, const float *pf, con
         const bool start = valid && s != sp;
         int f = 0;
         if (valid && s >= 0 && split_flag[s]) f = PRE ? pflag[i] : pf[(size_t)i * 4 * W + sdim[s]] < sval[s];
-        fbits |= (unsigned)f << j;
-        rbits |= (unsigned)start << j;
         const unsigned F = __ballot_sync(0xffffffffu, f), R = __ballot_sync(0xffffffffu, start);
         if (lane == 0) {
             const unsigned keep = R ? ~((1u << (31 - __clz(R))) - 1u) : 0xffffffffu;
             rowsum[j * PT_WARPS + warp] = seg_pack(R != 0, __popc(F & keep));
+            fword[j * PT_WARPS + warp] = F;
+            rword[j * PT_WARPS + warp] = R;
         }
     }
 }
+
+// Per tile: the segmented count (tsum), and for each of its PT_ROWS *
+// PT_WARPS warp-rows the flag ballot, the segment-start ballot and the
+// segmented exclusive prefix inside the tile (twords, 3 words per warp-row),
+// so that the move pass needs no flag of its own.
+constexpr int PT_WR = PT_ROWS * PT_WARPS;   // warp-rows per tile
+constexpr int PT_TW = 3 * PT_WR;            // stored words per tile
 
 template <int DC, bool PRE = false>
 __global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const float4 *__restrict__ P,
@@ -153,17 +158,40 @@ __global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const floa
                                                            const int *__restrict__ sdim,
                                                            const float *__restrict__ sval,
                                                            const int *__restrict__ T, unsigned *__restrict__ tsum,
+                                                           unsigned *__restrict__ twords,
                                                            const int *__restrict__ pflag = nullptr) {
     if (*T == 0) return;
-    __shared__ unsigned rowsum[PT_ROWS * PT_WARPS];
-    unsigned fbits, rbits;
-    tile_flags<DC, PRE>((int)n, blockIdx.x * PT_TILE, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval,
-                   fbits, rbits, rowsum, pflag);
+    __shared__ unsigned rowsum[PT_WR], fword[PT_WR], rword[PT_WR];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    tile_flags<DC, PRE>((int)n, blockIdx.x * PT_TILE, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim,
+                        sval, fword, rword, rowsum, pflag);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned a = 0;
-        for (int e = 0; e < PT_ROWS * PT_WARPS; ++e) a = seg_combine(a, rowsum[e]);
-        tsum[blockIdx.x] = a;
+    unsigned *tw = twords + (size_t)blockIdx.x * PT_TW;
+    if (warp == 0) {
+        constexpr int PER = PT_WR / 32;
+        unsigned loc = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) loc = seg_combine(loc, rowsum[lane * PER + k]);
+        unsigned x = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x = seg_combine(y, x);
+        }
+        unsigned in = __shfl_up_sync(0xffffffffu, x, 1);
+        if (lane == 0) in = 0u;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = lane * PER + k;
+            tw[2 * PT_WR + e] = in;
+            in = seg_combine(in, rowsum[e]);
+        }
+        if (lane == 31) tsum[blockIdx.x] = in;
+    } else if (warp == 1) {
+        for (int e = lane; e < PT_WR; e += 32) {
+            tw[e] = fword[e];
+            tw[PT_WR + e] = rword[e];
+        }
     }
 }
 
@@ -480,20 +508,18 @@ pg_status level_segments(int S_max, int *ctl, const Segs &cur, const Segs &nxt, 
 // and reduce the children's tight boxes: per tile in shared memory (children
 // of a tile are few and consecutive), then one global atomic per child and
 // dimension; a child that finds its slot taken goes straight to global memory.
-template <int DC, bool PRE = false>
+template <int DC>
 __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
                                                      const int *__restrict__ seg_of, int *__restrict__ seg_of_nx,
                                                      const int *__restrict__ start, const int *__restrict__ end,
                                                      const int *__restrict__ split_flag,
                                                      const int *__restrict__ split_rank,
-                                                     const int *__restrict__ sdim, const float *__restrict__ sval,
-                                                     const unsigned *__restrict__ tcarry, int *__restrict__ nx_start,
+                                                     const unsigned *__restrict__ tcarry,
+                                                     const unsigned *__restrict__ twords, int *__restrict__ nx_start,
                                                      int *__restrict__ nx_end, int *__restrict__ nx_lo,
-                                                     int *__restrict__ nx_hi, const int *__restrict__ T,
-                                                     const int *__restrict__ pflag = nullptr) {
+                                                     int *__restrict__ nx_hi, const int *__restrict__ T) {
     constexpr int W = bucket_w(DC);
     if (*T == 0) return;
-    __shared__ unsigned rowsum[PT_ROWS * PT_WARPS];
     __shared__ int tag[kBoxSlots];
     __shared__ int b_lo[kBoxSlots * DC], b_hi[kBoxSlots * DC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -504,33 +530,9 @@ __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n,
         b_lo[x] = 0x7f800000;
         b_hi[x] = (int)0x807fffffu;
     }
-    unsigned fbits, rbits;
-    tile_flags<DC, PRE>(n32, base, reinterpret_cast<const float *>(P), seg_of, split_flag, sdim, sval, fbits, rbits,
-                   rowsum, pflag);
     __syncthreads();
-    // segmented exclusive scan of the tile's warp-rows (warp 0, 4 per lane)
-    if (warp == 0) {
-        constexpr int PER = PT_ROWS * PT_WARPS / 32;
-        unsigned loc = 0;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) loc = seg_combine(loc, rowsum[lane * PER + k]);
-        unsigned x = loc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x = seg_combine(y, x);
-        }
-        unsigned in = __shfl_up_sync(0xffffffffu, x, 1);
-        if (lane == 0) in = 0u;
-        in = seg_combine(tcarry[blockIdx.x], in);
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const unsigned e = rowsum[lane * PER + k];
-            rowsum[lane * PER + k] = in;
-            in = seg_combine(in, e);
-        }
-    }
-    __syncthreads();
+    const unsigned *tw = twords + (size_t)blockIdx.x * PT_TW;
+    const unsigned carry = tcarry[blockIdx.x];
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < PT_ROWS; ++j) {
@@ -540,13 +542,13 @@ __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n,
 #pragma unroll
         for (int w = 0; w < W; ++w) v[w] = valid ? P[(size_t)i * W + w] : make_float4(0.f, 0.f, 0.f, 0.f);
         const int s = valid ? seg_of[i] : -1;
-        const int f = (fbits >> j) & 1u;
-        const unsigned F = __ballot_sync(0xffffffffu, f);
-        const unsigned R = __ballot_sync(0xffffffffu, (rbits >> j) & 1u);
+        const int e = j * PT_WARPS + warp;
+        const unsigned F = tw[e], R = tw[PT_WR + e];
+        const int f = (F >> lane) & 1u;
         const unsigned m = R & (lt | (1u << lane));
         int r;
         if (m) r = __popc(F & lt & ~((1u << (31 - __clz(m))) - 1u));
-        else r = (int)(rowsum[j * PT_WARPS + warp] & 0x7fffffffu) + __popc(F & lt);
+        else r = (int)(seg_combine(carry, tw[2 * PT_WR + e]) & 0x7fffffffu) + __popc(F & lt);
         int child = -1;
         if (valid) {
             int dst = i;
@@ -800,7 +802,8 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
     int *fin_flag = sdim + 2 * seg_cap;
     int *fin_rank = fin_flag + seg_cap;
     const int ntiles = std::max(1, ceil_div_i(n, PT_TILE));
-    PG_TRY(sBsum.alloc(sizeof(unsigned) * (size_t)ntiles, s));
+    PG_TRY(sBsum.alloc(sizeof(unsigned) * (size_t)ntiles * (1 + PT_TW), s));
+    unsigned *tsum = sBsum.as<unsigned>(), *twords = tsum + ntiles;
     PG_TRY(sCtl.alloc(sizeof(int) * CTL_WORDS, s));
     int *ctl = sCtl.as<int>();
     // segments handed to the block-scope finisher (disjoint, > leaf points each)
@@ -890,22 +893,20 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
             k_obj_first<<<g, BT, 0, s>>>((int)n, k2, sentinel, ofirst);
             k_obj_flags<DC><<<g, BT, 0, s>>>((int)n, k2, v2, sentinel, ofirst, cur.start, cur.end, split_rank, sdim, P,
                                             ctl, opflag, t->split_val);
-            k_part_tiles<DC, true><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T,
-                                                                 sBsum.as<unsigned>(), opflag);
-            k_part_carry<<<1, 1024, 0, s>>>(sBsum.as<unsigned>(), ntiles, T, ctl, fin_rank + S_max, level);
-            k_part<DC, true><<<ntiles, PT_THREADS, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
-                                                           split_rank, sdim, sval, sBsum.as<unsigned>(), nxt.start,
-                                                           nxt.end, nxt.lo, nxt.hi, T, opflag);
+            k_part_tiles<DC, true><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, tsum,
+                                                                 twords, opflag);
+            k_part_carry<<<1, 1024, 0, s>>>(tsum, ntiles, T, ctl, fin_rank + S_max, level);
+            k_part<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
+                                                     split_rank, tsum, twords, nxt.start, nxt.end, nxt.lo, nxt.hi, T);
             for (int c = 0; c < 5; ++c) count_launch();
         } else {
-            k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, sBsum.as<unsigned>());
-            k_part_carry<<<1, 1024, 0, s>>>(sBsum.as<unsigned>(), ntiles, T, ctl, fin_rank + S_max, level);
+            k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, tsum, twords);
+            k_part_carry<<<1, 1024, 0, s>>>(tsum, ntiles, T, ctl, fin_rank + S_max, level);
             count_launch();
             count_launch();
             KTimer kt("build_scatter", s);
             k_part<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
-                                                     split_rank, sdim, sval, sBsum.as<unsigned>(), nxt.start, nxt.end,
-                                                     nxt.lo, nxt.hi, T);
+                                                     split_rank, tsum, twords, nxt.start, nxt.end, nxt.lo, nxt.hi, T);
             count_launch();
         }
         PG_TRY(check_launch("build level"));
@@ -1026,11 +1027,12 @@ pg_status forest_levels_impl(const ForestArgs &fa, cudaStream_t s) {
                                   fin_rank, fin, fa.nodes, fa.n_sdim, fa.n_sval, fa.n_range, fa.n_parent, fa.roots, 1,
                                   fa.scan_ws, s));
         const int *T = split_rank + S_max;
-        k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(fa.n, P, seg_of, split_flag, sdim, sval, T, fa.tiles);
+        unsigned *twords = fa.tiles + ntiles;
+        k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(fa.n, P, seg_of, split_flag, sdim, sval, T, fa.tiles, twords);
         k_part_carry<<<1, 1024, 0, s>>>(fa.tiles, ntiles, T, fa.ctl, fin_rank + S_max, level);
         k_part<DC><<<ntiles, PT_THREADS, 0, s>>>(fa.n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
-                                                 split_rank, sdim, sval, fa.tiles, nxt.start, nxt.end, nxt.lo,
-                                                 nxt.hi, T);
+                                                 split_rank, fa.tiles, twords, nxt.start, nxt.end, nxt.lo, nxt.hi,
+                                                 T);
         count_launch();
         count_launch();
         count_launch();
@@ -1059,8 +1061,8 @@ pg_status pack_impl(const float *src, const int32_t *rows, const int32_t *ids, i
 
 int64_t forest_words(int dc, int seg_cap, int fin_cap, int64_t n) {
     const int64_t ntiles = std::max<int64_t>(1, (n + PT_TILE - 1) / PT_TILE);
-    return 2 * (int64_t)seg_cap * (5 + 2 * dc) + 6 * (int64_t)seg_cap + 2 + (int64_t)fin_cap * (5 + 2 * dc) + ntiles +
-           CTL_WORDS + scan_ws_words(seg_cap) + 64;
+    return 2 * (int64_t)seg_cap * (5 + 2 * dc) + 6 * (int64_t)seg_cap + 2 + (int64_t)fin_cap * (5 + 2 * dc) +
+           ntiles * (1 + PT_TW) + CTL_WORDS + scan_ws_words(seg_cap) + 64;
 }
 
 void forest_carve(ForestArgs &fa, int *words, int dc) {
@@ -1069,7 +1071,8 @@ void forest_carve(ForestArgs &fa, int *words, int dc) {
     fa.seg_b = p; p += (size_t)fa.seg_cap * (5 + 2 * dc);
     fa.lvl = p; p += 6 * (size_t)fa.seg_cap + 2;
     fa.fin = p; p += (size_t)fa.fin_cap * (5 + 2 * dc);
-    fa.tiles = reinterpret_cast<unsigned *>(p); p += std::max<int64_t>(1, (fa.n + PT_TILE - 1) / PT_TILE);
+    fa.tiles = reinterpret_cast<unsigned *>(p);
+    p += std::max<int64_t>(1, (fa.n + PT_TILE - 1) / PT_TILE) * (1 + PT_TW);
     fa.ctl = p; p += CTL_WORDS;
     fa.scan_ws = p;
 }
