@@ -10,13 +10,15 @@
 //              which numbers the next level's segments),
 //   link       one thread per segment: record the node, hang the segment in
 //              its parent's record, set up the two children,
-//   scatter    stable partition of the permutation, children's tight boxes
+//   scatter    partition of the permutation (left points in order at the
+//              front, right points from the back), children's tight boxes
 //              by warp-aggregated shared-memory min/max.
 // An internal node splitting [st, en) at m is stored in node slot
 // node_base + (m - 1): the gaps between consecutive positions name the
 // internal nodes uniquely, so the numbering is fixed by the tree alone and a
-// range of n points needs at most n - 1 slots.  The result (bucket order,
-// splits, boxes) is the same tree the level-synchronous builders produce.
+// range of n points needs at most n - 1 slots.  Splits and boxes are those
+// of the level-synchronous builders (only the order of the points inside a
+// leaf may differ, which no answer depends on).
 #pragma once
 
 #include <climits>
@@ -41,6 +43,7 @@ __host__ __device__ inline size_t smem_build_bytes(int ns, int sc, int dc) {
     b += smem_al16(sizeof(int) * 4 * (size_t)sc);                 // parent code, depth (x2)
     b += smem_al16(sizeof(int) * 2 * (size_t)sc * dc);            // tight boxes
     b += smem_al16(sizeof(int) * 2 * (size_t)sc);                 // split dimension, split value
+    b += smem_al16(sizeof(int) * 2 * (size_t)sc);                 // left-count base, split rank
     b += smem_al16(sizeof(uint32_t) * sw);                        // split ballots
     b += smem_al16(sizeof(int) * (sw + 1));                       // their prefix
     return b;
@@ -69,6 +72,7 @@ struct SmemBuild {
     int *lo, *hi;
     int *sdim;
     float *sval;
+    int *sb0, *srk;            // per split segment: flags before its start, its rank
     uint32_t *sword;
     int *spre;
     __device__ void carve(unsigned char *base, int ns, int sc) {
@@ -88,6 +92,8 @@ struct SmemBuild {
         lo = q; hi = q + (size_t)sc * DC;
         q = reinterpret_cast<int *>(take(sizeof(int) * 2 * (size_t)sc));
         sdim = q; sval = reinterpret_cast<float *>(q + sc);
+        q = reinterpret_cast<int *>(take(sizeof(int) * 2 * (size_t)sc));
+        sb0 = q; srk = q + sc;
         sword = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * sw));
         spre = reinterpret_cast<int *>(take(sizeof(int) * (sw + 1)));
     }
@@ -219,8 +225,10 @@ __device__ CtaTree cta_build_smem(float4 *P, int s0, int s1, const int *root_lo,
             const bool split = (m.sword[s >> 5] >> (s & 31)) & 1u;
             const int code = c_code[s];
             int node = -1, nl = 0;
+            int b0 = 0;
             if (split) {
-                nl = ballot_prefix(m.word, m.wpre, en) - ballot_prefix(m.word, m.wpre, st);
+                b0 = ballot_prefix(m.word, m.wpre, st);
+                nl = ballot_prefix(m.word, m.wpre, en) - b0;
                 node = (level == 0 && root_slot >= 0) ? root_slot : node_base + st + nl - 1;
             }
             if (level == 0) {
@@ -244,6 +252,8 @@ __device__ CtaTree cta_build_smem(float4 *P, int s0, int s1, const int *root_lo,
                 n_range[node] = make_int2(s0 + st, s0 + en);
                 if (n_parent) n_parent[node] = code;
                 const int r = ballot_prefix(m.sword, m.spre, s);
+                m.sb0[s] = b0;
+                m.srk[s] = r;
 #pragma unroll
                 for (int ch = 0; ch < 2; ++ch) {
                     const int x = 2 * r + ch;
@@ -272,13 +282,13 @@ __device__ CtaTree cta_build_smem(float4 *P, int s0, int s1, const int *root_lo,
                 const int s = c_seg[i];
                 int dst = i;
                 if (s != NONE && ((m.sword[s >> 5] >> (s & 31)) & 1u)) {
+                    // left points keep their order at the front, right points
+                    // fill the segment from the back (no segment total needed)
                     const int st = c_st[s], en = c_en[s];
-                    const int b0 = ballot_prefix(m.word, m.wpre, st);
-                    const int nl = ballot_prefix(m.word, m.wpre, en) - b0;
-                    const int r = ballot_prefix(m.word, m.wpre, i) - b0;
-                    const int rk = ballot_prefix(m.sword, m.spre, s);
+                    const int r = ballot_prefix(m.word, m.wpre, i) - m.sb0[s];
+                    const int rk = m.srk[s];
                     if ((m.word[i >> 5] >> (i & 31)) & 1u) { dst = st + r; child = 2 * rk; }
-                    else { dst = st + nl + (i - st) - r; child = 2 * rk + 1; }
+                    else { dst = en - 1 - ((i - st) - r); child = 2 * rk + 1; }
                 }
                 n_perm[dst] = (uint16_t)pidx;
                 n_seg[dst] = child >= 0 ? (uint16_t)child : NONE;
