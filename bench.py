@@ -136,9 +136,9 @@ KNN_SOURCES = ["knn_kernel.cuh", "common.cuh", "knn_dc3.cu"]
 KNN_KERNELS = {1: "k_knn", 2: "k_knn_packet", 3: "k_knn_ww"}
 
 
-def traffic_for(kernel: str, sha: str, units: int, variant: int, leaf: int):
-    """ncu DRAM bytes per launch from profiles/, if taken on this kernel source
-    with the same traversal variant and leaf size."""
+def traffic_record(kernel: str, sha: str, variant: int, leaf: int):
+    """The ncu record in profiles/ (DRAM bytes per unit, cache hit rates), if
+    taken on this kernel source with the same traversal variant and leaf size."""
     path = os.path.join(ROOT, "profiles", f"{kernel}.traffic.json")
     try:
         d = json.load(open(path))
@@ -146,7 +146,7 @@ def traffic_for(kernel: str, sha: str, units: int, variant: int, leaf: int):
         return None
     if d.get("source_sha") != sha or d.get("variant") != variant or d.get("leaf") != leaf:
         return None
-    return float(d["dram_bytes_per_unit"]) * units
+    return d
 
 
 def cpu_baseline(pts, k, budget_s=12.0):
@@ -166,7 +166,8 @@ def cpu_baseline(pts, k, budget_s=12.0):
     oracle.knn(pts, sample, k, nthreads=threads)
     dt = time.perf_counter() - t0
     return {"value": m / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{m} all-kNN queries (k={k}) against all {n} points, float64 brute force"}
+            "sample": f"{m} all-kNN queries (k={k}) against all {n} points, float64 brute force",
+            "extrapolated_full_run_s": n / (m / dt)}
 
 
 def batched_vs_plain(api, torch, dev, k: int, reps: int = 3):
@@ -610,7 +611,8 @@ def run_ours(args):
     knn_avg_ms = knn_ms / max(knn_launches, 1)
     achieved = alg_bytes / (knn_avg_ms / 1e3) / 1e9
     sha = kernel_sha(KNN_SOURCES)
-    traffic = traffic_for("knn_traverse", sha, n, variant, leaf)
+    rec = traffic_record("knn_traverse", sha, variant, leaf)
+    traffic = None if rec is None else float(rec["dram_bytes_per_unit"]) * n
     # touched-bytes model: node records and bucket entries the traversal loads
     # (through L1/L2), counted by the counting instance of the same kernel in
     # one extra launch outside the timed region
@@ -633,6 +635,9 @@ def run_ours(args):
                 "touched_frac": None if touched is None else touched / (knn_avg_ms / 1e3) / 1e9 / peak,
                 "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": knn_avg_ms, "launches_timed": knn_launches, "source_sha": sha}
+    if rec is not None and "l2_sector_hit_pct" in rec:
+        roofline["cache_hit_pct"] = {"l2": rec["l2_sector_hit_pct"], "l2_reads": rec["l2_read_sector_hit_pct"],
+                                     "l1": rec["l1_sector_hit_pct"], "source": "ncu, profiles/"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -56,6 +56,10 @@ TREE_CASES = {
     "depth_cap_chain": (lambda: _chain_1d(120), 1),
     "leaf1": (lambda: synth.uniform(3000, 2, 12), 1),
     "negative_coords": (lambda: synth.uniform(4000, 3, 13) - 0.5, 16),
+    # several hundred 2048-point partition tiles: the upper levels' segments
+    # span many tiles, so the carry into a tile is found across look-back windows
+    "uniform3d_600k_leaf48": (lambda: synth.uniform(600000, 3, 14), 48),
+    "gmm3d_400k_leaf16": (lambda: synth.gmm(400000, 3, 15), 16),
 }
 
 
