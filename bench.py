@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-extras", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--extras-only", default="", metavar="NAMES",
+                   help="time only these other workloads, comma separated: 2d, graph_range, object, gmm, bdl "
+                        "(for profiling)")
     p.add_argument("--batched-only", type=int, default=0, metavar="K",
                    help="time only the batched Chamfer forward + backward with this k (for profiling)")
     return p.parse_args()
@@ -264,40 +267,10 @@ def batched_only(args):
                       "fwd_ms": statistics.median(fwd), "bwd_ms": statistics.median(bwd)}), flush=True)
 
 
-def other_configs(api, torch, dev):
-    """Timings of the other workloads (CUDA events, one warm-up each); these
-    are reported beside the headline, their parity is covered by the tests."""
+def graph_range(api, torch, dev, timed, out):
+    """k-NN graph and range search timings on 10M uniform 2D points."""
     from paper_2207_01834_gb300 import synth
 
-    stream = torch.cuda.current_stream()
-
-    def timed(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        best = float("inf")
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            best = min(best, e0.elapsed_time(e1))
-        return best
-
-    out = {}
-    # 2D all-kNN, 20,000 uniform points, leaf 16, k = 5
-    x = torch.from_numpy(synth.uniform(20000, 2, synth.BASE_SEED)).to(dev)
-    holder = {}
-
-    def b2():
-        holder["t"] = api.pg_tree_build(x, 16)
-
-    def q2():
-        api.pg_knn(holder["t"], None, 5)
-
-    bms = timed(b2)
-    qms = timed(q2)
-    out["2d_20k_k5"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 20000 / qms / 1e3}
     # k-NN graph of 10,000,000 uniform 2D points, k = 10 (the paper's Table 1
     # k-NN graph workload is 2D 10M; its k is not stated)
     xg = torch.from_numpy(synth.uniform(10_000_000, 2, synth.BASE_SEED + 9)).to(dev)
@@ -323,8 +296,62 @@ def other_configs(api, torch, dev):
     out["range_2d_10m_all_r_for_10"] = {"radius": radius, "range_ms": rms, "results": int(hg["r"][0].numel())}
     tg.free()
     del xg, hg
-    # object-median split (the paper's other split rule) on the headline set:
-    # 10M uniform 3D points, all-kNN k = 10, leaf 48, postponed-leaf traversal
+
+
+EXTRAS = ("2d", "graph_range", "object", "gmm", "bdl")
+
+
+def other_configs(api, torch, dev, only=None):
+    """Timings of the other workloads (CUDA events, one warm-up each); these
+    are reported beside the headline, their parity is covered by the tests.
+    `only`: a subset of EXTRAS to run (all by default)."""
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    out = {}
+    sections = {"2d": small_2d, "graph_range": graph_range, "object": object_median, "gmm": gmm_5d_7d,
+                "bdl": bdl_schedule}
+    for name in EXTRAS:
+        if only is None or name in only:
+            sections[name](api, torch, dev, timed, out)
+    return out
+
+
+def small_2d(api, torch, dev, timed, out):
+    """2D all-kNN, 20,000 uniform points, leaf 16, k = 5."""
+    from paper_2207_01834_gb300 import synth
+
+    x = torch.from_numpy(synth.uniform(20000, 2, synth.BASE_SEED)).to(dev)
+    holder = {}
+
+    def b2():
+        holder["t"] = api.pg_tree_build(x, 16)
+
+    def q2():
+        api.pg_knn(holder["t"], None, 5)
+
+    bms = timed(b2)
+    qms = timed(q2)
+    out["2d_20k_k5"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 20000 / qms / 1e3}
+
+
+def object_median(api, torch, dev, timed, out):
+    """Object-median split (the paper's other split rule) on the headline set:
+    10M uniform 3D points, all-kNN k = 10, leaf 48, postponed-leaf traversal."""
+    from paper_2207_01834_gb300 import synth
+
     xo = torch.from_numpy(synth.uniform(10_000_000, 3, synth.BASE_SEED + 2)).to(dev)
     ho = {}
 
@@ -339,10 +366,13 @@ def other_configs(api, torch, dev):
     oqms = timed(qo)
     ho["t"].free()
     out["object_median_3d_10m_k10"] = {"build_ms": obms, "knn_ms": oqms, "knn_mqps": 1e7 / oqms / 1e3}
-    del xo, ho
-    # 5D / 7D clustered: 2,000,000 points, 1,000,000 separate queries, k = 16
-    # (leaf size and traversal variant autotuned on the workload itself)
-    from paper_2207_01834_gb300 import autotune
+
+
+def gmm_5d_7d(api, torch, dev, timed, out):
+    """5D / 7D clustered: 2,000,000 points, 1,000,000 separate queries, k = 16
+    (leaf size and traversal variant autotuned on the workload itself)."""
+    from paper_2207_01834_gb300 import autotune, synth
+
     for d in (5, 7):
         mix = synth.gmm_mixture(d, synth.BASE_SEED + 3)
         pts = torch.from_numpy(synth.gmm_sample(2_000_000, mix, synth.BASE_SEED + 30 + d)).to(dev)
@@ -361,7 +391,14 @@ def other_configs(api, torch, dev):
         out[f"{d}d_gmm_2m_1mq_k16"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 1e6 / qms / 1e3,
                                        "leaf_size": leaf_d, "traversal_variant": var_d}
         h["t"].free()
-    # batch-dynamic BDL schedule (3D uniform, buffer 65,536, k = 10 queries after every batch)
+
+
+def bdl_schedule(api, torch, dev, timed, out):
+    """Batch-dynamic BDL schedule (3D uniform, buffer 65,536, k = 10 queries
+    after every batch)."""
+    from paper_2207_01834_gb300 import synth
+
+    stream = torch.cuda.current_stream()
     f = api.BDL(3, 65536, 16)
     g = np.random.default_rng(77)
     chunks, live = [], np.zeros(0, bool)
@@ -396,7 +433,6 @@ def other_configs(api, torch, dev):
                                  "forest_knn_mqps_mean": 1e6 / float(np.mean(q_ms)) / 1e3,
                                  "live_points_end": int(f.size())}
     f.free()
-    return out
 
 
 def combine_ranks(dist, device, local_ms: float, units_per_rank: float, ws: int):
@@ -661,10 +697,28 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def extras_only(names):
+    """Only the named other workloads (one JSON line), for profiling."""
+    import torch
+
+    from paper_2207_01834_gb300 import api
+
+    only = [x for x in names.split(",") if x]
+    unknown = [x for x in only if x not in EXTRAS]
+    if unknown:
+        raise SystemExit(f"unknown workloads {unknown}; choose from {', '.join(EXTRAS)}")
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    print(json.dumps({"other_configs": other_configs(api, torch, dev, only=only)}), flush=True)
+
+
 def main():
     args = parse()
     if args.batched_only > 0:
         batched_only(args)
+        return
+    if args.extras_only:
+        extras_only(args.extras_only)
         return
     if args.impl == "reference":
         run_reference(args)

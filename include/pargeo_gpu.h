@@ -49,7 +49,7 @@ typedef enum {
     PG_ENOMEM = 2,        /* device or host allocation failed                 */
     PG_ECUDA = 3,         /* a CUDA runtime call failed                       */
     PG_ETIMEOUT = 4,      /* a bounded device-side wait gave up               */
-    PG_EUNSUPPORTED = 5   /* valid request this build does not support        */
+    PG_EUNSUPPORTED = 5   /* valid request the library does not support       */
 } pg_status;
 
 typedef struct pg_tree pg_tree;   /* one static kd-tree (opaque)                */

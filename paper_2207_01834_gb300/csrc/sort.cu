@@ -2,7 +2,9 @@
 // pairs, 8 bits per pass.  Each pass: per-tile digit histograms, one
 // device-wide exclusive scan over the digit-major histogram table, then a
 // stable scatter in which every tile ranks its items in input order (warp
-// match + popcount, then per-digit offsets across the tile's warps).
+// match + popcount, then per-digit offsets across the tile's warps), puts
+// them in that order in shared memory, and writes each digit's run to its
+// global range with consecutive threads on consecutive addresses.
 #include "internal.h"
 #include "sort.h"
 
@@ -15,6 +17,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kRounds = 8;                    // items per thread
 constexpr int kTile = kThreads * kRounds;     // 2048 items per tile
 constexpr int kRadix = 256;
+static_assert(kThreads == kRadix, "one thread per digit in the scatter's tile scan");
 
 __global__ void __launch_bounds__(kThreads) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
                                                       int ntiles, int *__restrict__ ghist) {
@@ -36,7 +39,8 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t *__restr
                                                          int ntiles, const int *__restrict__ goff,
                                                          uint32_t *__restrict__ okeys, uint32_t *__restrict__ ovals) {
     __shared__ int wcnt[kWarps][kRadix];
-    __shared__ int toff[kRadix];
+    __shared__ int toff[kRadix], lstart[kRadix], wsum[kWarps];
+    __shared__ uint32_t sk[kTile], sv[kTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wcnt[0][0])[i] = 0;
     toff[threadIdx.x] = goff[(int64_t)threadIdx.x * ntiles + blockIdx.x];
@@ -62,6 +66,8 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t *__restr
     }
     __syncthreads();
     {
+        // per digit (thread = digit): offsets of the warps' runs, the tile's
+        // count, and the exclusive scan of the counts over the digits
         int run = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
@@ -69,16 +75,39 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t *__restr
             wcnt[w][threadIdx.x] = run;
             run += c;
         }
+        int x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        lstart[threadIdx.x] = before + x - run;
     }
     __syncthreads();
+    // the tile in stable digit order in shared memory
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const int d = d_[r];
         if (d < kRadix) {
-            const int pos = toff[d] + wcnt[warp][d] + rank[r];
-            okeys[pos] = k_[r];
-            ovals[pos] = v_[r];
+            const int lp = lstart[d] + wcnt[warp][d] + rank[r];
+            sk[lp] = k_[r];
+            sv[lp] = v_[r];
         }
+    }
+    __syncthreads();
+    // item j of the tile goes to its digit's global offset + its place in the run
+    const int64_t tb = (int64_t)blockIdx.x * kTile;
+    const int tn = (int)min((int64_t)kTile, n - tb);
+    for (int j = threadIdx.x; j < tn; j += kThreads) {
+        const uint32_t kk = sk[j];
+        const int d = (int)((kk >> shift) & 0xff);
+        const int pos = toff[d] + (j - lstart[d]);
+        okeys[pos] = kk;
+        ovals[pos] = sv[j];
     }
 }
 
