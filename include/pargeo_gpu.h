@@ -195,6 +195,26 @@ PG_API pg_status pg_range(const pg_tree *tree, const float *queries, int64_t m, 
                           int32_t *out_idx, int64_t *out_offsets, int64_t *out_total, void *stream);
 
 /*
+ * Range search, second half: writes the result rows of the search that a
+ * pg_range call with out_idx == NULL sized (same tree, queries, m and radius)
+ * from the offsets that call returned, without counting again.  Same rows as
+ * pg_range with out_idx would write.
+ *   offsets      device, m + 1 int64, as pg_range wrote them.
+ *   capacity     int32 slots in out_idx (at least offsets[m]).
+ *   out_idx      device; row i goes to out_idx[offsets[i] .. offsets[i+1]).
+ * Nothing is written outside a row's own offsets or at or above capacity,
+ * whatever the offsets hold.  Stream-ordered; synchronises the stream once to
+ * read the row check.  Errors: PG_EINVAL (NULL tree, NULL offsets or out_idx
+ * with m > 0 and n > 0, m out of [0, 2^31), queries NULL with m != n, radius
+ * negative or not finite, capacity < 0, or a row whose point count differs
+ * from its offsets or does not fit below capacity: the offsets do not belong
+ * to this search, and such rows are incomplete); PG_ENOMEM for scratch
+ * (4 * m + 4 bytes).
+ */
+PG_API pg_status pg_range_fill(const pg_tree *tree, const float *queries, int64_t m, float radius,
+                               const int64_t *offsets, int64_t capacity, int32_t *out_idx, void *stream);
+
+/*
  * Traversal variant used by pg_knn and pg_bdl_knn for every later call in this
  * process (App. A.1.3 searches each query independently; every variant returns
  * that same exact answer): 1 = one thread per query walks its own path;

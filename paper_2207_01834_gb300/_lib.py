@@ -49,6 +49,7 @@ SIGNATURES = {
     "pg_knn_set_variant": (_S, [_I]),
     "pg_knn_graph": (_S, [_P, _I, _I64, _P, C.POINTER(_I64), _P]),
     "pg_range": (_S, [_P, _P, _I64, C.c_float, _I64, _P, _P, C.POINTER(_I64), _P]),
+    "pg_range_fill": (_S, [_P, _P, _I64, C.c_float, _P, _I64, _P, _P]),
     "pg_knn_touch_enable": (_S, [_I]),
     "pg_knn_touch_read": (_S, [C.POINTER(_I64), C.POINTER(_I64)]),
     "pg_bdl_create": (_S, [_I, _I64, _I, _P, C.POINTER(_P)]),

@@ -172,8 +172,7 @@ def pg_range(tree: Tree, queries: torch.Tensor | None, radius: float, stream=Non
     total = C.c_int64()
     call("pg_range", tree.handle, qp, m, float(radius), 0, None, _ptr(offsets), C.byref(total), _stream(stream))
     idx = torch.empty(max(total.value, 1), dtype=torch.int32, device=tree.device)
-    call("pg_range", tree.handle, qp, m, float(radius), idx.numel(), _ptr(idx), _ptr(offsets), C.byref(total),
-         _stream(stream))
+    call("pg_range_fill", tree.handle, qp, m, float(radius), _ptr(offsets), idx.numel(), _ptr(idx), _stream(stream))
     return idx[:total.value], offsets
 
 

@@ -9,7 +9,10 @@
 // a point inside the box, so nothing inside the ball is skipped).  Two passes
 // make the output deterministic without atomics: the first counts each
 // query's points, an exclusive scan turns the counts into row offsets, and
-// the second writes each row's indices in the order of the walk.
+// the second writes each row's indices in the order of the walk.  The fill
+// pass writes a row only inside its offsets and below the capacity, and flags
+// a row whose count differs from them, so offsets from another call can
+// never make it write out of bounds.
 #include <algorithm>
 
 #include "internal.h"
@@ -25,8 +28,9 @@ template <int DC, bool FILL>
 __global__ void __launch_bounds__(RT) k_range(const TreeDesc *__restrict__ trees, const float *__restrict__ queries,
                                               const float4 *__restrict__ self_bucket,
                                               const int32_t *__restrict__ order, int64_t m, int dim, float r2,
-                                              int *__restrict__ counts, const int *__restrict__ offs,
-                                              int32_t *__restrict__ out_idx) {
+                                              int *__restrict__ counts, const int64_t *__restrict__ offs,
+                                              int64_t capacity, int32_t *__restrict__ out_idx,
+                                              int *__restrict__ bad) {
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= m) return;
     constexpr int NW = node_w(DC);
@@ -42,15 +46,19 @@ __global__ void __launch_bounds__(RT) k_range(const TreeDesc *__restrict__ trees
 #pragma unroll
         for (int c = 0; c < DC; ++c) q[c] = c < dim ? queries[row * dim + c] : 0.f;
     }
-    int found = 0;
-    int32_t *out = FILL ? out_idx + offs[row] : nullptr;
+    int64_t found = 0, o0 = 0, o1 = 0, lim = 0;
+    if (FILL) {
+        o0 = offs[row];
+        o1 = offs[row + 1];
+        lim = o0 < 0 ? 0 : max((int64_t)0, min(o1, capacity) - o0);
+    }
     auto scan = [&](int ref, int cnt) {
         for (int i = ref; i < ref + cnt; ++i) {
             float p[DC];
             unsigned pid;
             load_point<DC>(T.bucket, i, p, pid);
             if (sqdist<DC>(q, p) <= r2) {
-                if (FILL) out[found] = (int32_t)pid;
+                if (FILL && found < lim) out_idx[o0 + found] = (int32_t)pid;
                 ++found;
             }
         }
@@ -88,7 +96,8 @@ __global__ void __launch_bounds__(RT) k_range(const TreeDesc *__restrict__ trees
             }
         }
     }
-    if (!FILL) counts[row] = found;
+    if (!FILL) counts[row] = (int)found;
+    else if (bad && (found != o1 - o0 || found > lim)) atomicExch(bad, 1);
 }
 
 __global__ void k_range_total(const int *__restrict__ counts, int64_t m, unsigned long long *__restrict__ total) {
@@ -105,33 +114,54 @@ __global__ void k_range_offsets(const int *__restrict__ pre, int64_t m, int64_t 
     if (i <= m) offsets[i] = pre[i];
 }
 
+// One pass: fill == false counts each query's points into counts; fill ==
+// true writes the rows given by offs (m + 1 int64) into out_idx.
+struct RangePass {
+    int *counts = nullptr;
+    const int64_t *offs = nullptr;
+    int64_t capacity = 0;
+    int32_t *out_idx = nullptr;
+    int *bad = nullptr;
+    bool fill = false;
+};
+
 template <int DC>
-pg_status range_pass(const pg_tree *t, const float *queries, const int32_t *order, int64_t m, float r2, int *counts,
-                     const int *offs, int32_t *out_idx, bool fill, cudaStream_t s) {
+pg_status range_pass(const pg_tree *t, const float *queries, const int32_t *order, int64_t m, float r2,
+                     const RangePass &a, cudaStream_t s) {
     const int grid = std::max(1, ceil_div_i(m, RT));
     const float4 *self = queries ? nullptr : t->bucket;
-    if (fill)
-        k_range<DC, true><<<grid, RT, 0, s>>>(t->desc, queries, self, order, m, t->dim, r2, counts, offs, out_idx);
+    if (a.fill)
+        k_range<DC, true><<<grid, RT, 0, s>>>(t->desc, queries, self, order, m, t->dim, r2, a.counts, a.offs,
+                                               a.capacity, a.out_idx, a.bad);
     else
-        k_range<DC, false><<<grid, RT, 0, s>>>(t->desc, queries, self, order, m, t->dim, r2, counts, offs, out_idx);
+        k_range<DC, false><<<grid, RT, 0, s>>>(t->desc, queries, self, order, m, t->dim, r2, a.counts, a.offs,
+                                                a.capacity, a.out_idx, a.bad);
     count_launch();
     return check_launch("range search");
 }
 
 pg_status range_dispatch(const pg_tree *t, const float *queries, const int32_t *order, int64_t m, float r2,
-                         int *counts, const int *offs, int32_t *out_idx, bool fill, cudaStream_t s) {
+                         const RangePass &a, cudaStream_t s) {
     switch (t->dc) {
-        case 2: return range_pass<2>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
-        case 3: return range_pass<3>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
-        case 4: return range_pass<4>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
-        case 5: return range_pass<5>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
-        case 6: return range_pass<6>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
-        case 7: return range_pass<7>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
-        case 8: return range_pass<8>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
-        case 12: return range_pass<12>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
-        case 16: return range_pass<16>(t, queries, order, m, r2, counts, offs, out_idx, fill, s);
+        case 2: return range_pass<2>(t, queries, order, m, r2, a, s);
+        case 3: return range_pass<3>(t, queries, order, m, r2, a, s);
+        case 4: return range_pass<4>(t, queries, order, m, r2, a, s);
+        case 5: return range_pass<5>(t, queries, order, m, r2, a, s);
+        case 6: return range_pass<6>(t, queries, order, m, r2, a, s);
+        case 7: return range_pass<7>(t, queries, order, m, r2, a, s);
+        case 8: return range_pass<8>(t, queries, order, m, r2, a, s);
+        case 12: return range_pass<12>(t, queries, order, m, r2, a, s);
+        case 16: return range_pass<16>(t, queries, order, m, r2, a, s);
         default: return fail(PG_EUNSUPPORTED, "dimension class");
     }
+}
+
+pg_status range_args(const pg_tree *tree, const float *queries, int64_t m, float radius, int64_t capacity) {
+    if (m < 0 || m >= (int64_t)1 << 31) return fail(PG_EINVAL, "range search: m must be in [0, 2^31)");
+    if (!queries && m != tree->n) return fail(PG_EINVAL, "range search: all-points search (queries == NULL) needs m == n");
+    if (!(radius >= 0.f && radius <= 3.4e38f)) return fail(PG_EINVAL, "range search: radius must be finite and >= 0");
+    if (capacity < 0) return fail(PG_EINVAL, "range search: capacity must be >= 0");
+    return PG_OK;
 }
 
 }  // namespace
@@ -143,10 +173,7 @@ using namespace pg;
 extern "C" pg_status pg_range(const pg_tree *tree, const float *queries, int64_t m, float radius, int64_t capacity,
                               int32_t *out_idx, int64_t *out_offsets, int64_t *out_total, void *stream) {
     if (!tree || !out_offsets || !out_total) return fail(PG_EINVAL, "pg_range: NULL argument");
-    if (m < 0 || m >= (int64_t)1 << 31) return fail(PG_EINVAL, "pg_range: m must be in [0, 2^31)");
-    if (!queries && m != tree->n) return fail(PG_EINVAL, "pg_range: all-points search (queries == NULL) needs m == n");
-    if (!(radius >= 0.f && radius <= 3.4e38f)) return fail(PG_EINVAL, "pg_range: radius must be finite and >= 0");
-    if (capacity < 0) return fail(PG_EINVAL, "pg_range: capacity must be >= 0");
+    PG_TRY(range_args(tree, queries, m, radius, capacity));
     *out_total = 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (m == 0) {
@@ -167,7 +194,9 @@ extern "C" pg_status pg_range(const pg_tree *tree, const float *queries, int64_t
         PG_TRY(query_order(tree, queries, m, tree->dim, ord.as<int32_t>(), s));
     }
     const int32_t *order = sorted ? ord.as<int32_t>() : nullptr;
-    PG_TRY(range_dispatch(tree, queries, order, m, r2, counts, nullptr, nullptr, false, s));
+    RangePass cp;
+    cp.counts = counts;
+    PG_TRY(range_dispatch(tree, queries, order, m, r2, cp, s));
     PG_TRY(tot.alloc(sizeof(unsigned long long), s));
     PG_CUDA(cudaMemsetAsync(tot.p, 0, sizeof(unsigned long long), s));
     k_range_total<<<std::min(ceil_div_i(m, 256), num_sms() * 8), 256, 0, s>>>(counts, m, tot.as<unsigned long long>());
@@ -182,5 +211,38 @@ extern "C" pg_status pg_range(const pg_tree *tree, const float *queries, int64_t
     count_launch();
     if (!out_idx) return check_launch("range offsets");
     if (capacity < (int64_t)total) return fail(PG_EINVAL, "pg_range: capacity is below the result count");
-    return range_dispatch(tree, queries, order, m, r2, counts, pre, out_idx, true, s);
+    RangePass fp;
+    fp.offs = out_offsets;
+    fp.capacity = capacity;
+    fp.out_idx = out_idx;
+    fp.fill = true;
+    return range_dispatch(tree, queries, order, m, r2, fp, s);
+}
+
+extern "C" pg_status pg_range_fill(const pg_tree *tree, const float *queries, int64_t m, float radius,
+                                   const int64_t *offsets, int64_t capacity, int32_t *out_idx, void *stream) {
+    if (!tree) return fail(PG_EINVAL, "pg_range_fill: NULL tree");
+    PG_TRY(range_args(tree, queries, m, radius, capacity));
+    if (m == 0 || tree->n == 0) return PG_OK;   // every row is empty
+    if (!offsets || !out_idx) return fail(PG_EINVAL, "pg_range_fill: NULL offsets or out_idx");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Scratch ord, flag;
+    PG_TRY(flag.alloc(sizeof(int), s));
+    PG_TRY(fill_words(flag.p, 0u, 1, s));
+    const bool sorted = queries && m >= kOrderMinQueries;
+    if (sorted) {
+        PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)m, s));
+        PG_TRY(query_order(tree, queries, m, tree->dim, ord.as<int32_t>(), s));
+    }
+    RangePass fp;
+    fp.offs = offsets;
+    fp.capacity = capacity;
+    fp.out_idx = out_idx;
+    fp.bad = flag.as<int>();
+    fp.fill = true;
+    PG_TRY(range_dispatch(tree, queries, sorted ? ord.as<int32_t>() : nullptr, m, radius * radius, fp, s));
+    int bad = 0;
+    PG_TRY(read_small(&bad, flag.p, sizeof(int), s));
+    if (bad) return fail(PG_EINVAL, "pg_range_fill: the offsets do not match this tree, query set and radius");
+    return PG_OK;
 }

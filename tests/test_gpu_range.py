@@ -97,3 +97,38 @@ def test_range_errors(api):
              None)
     assert e.value.status == PG_EINVAL
     t.free()
+
+
+def test_range_fill_matches_one_call_and_rejects_foreign_offsets(api):
+    import ctypes as C
+    from paper_2207_01834_gb300._lib import PG_EINVAL, PgError, call
+
+    pts = synth.gmm(20000, 3, 89)
+    q = _cuda(synth.uniform(5000, 3, 90))        # >= 4096: the leaf-ordered path
+    t = api.pg_tree_build(_cuda(pts), leaf_size=16)
+    offs = torch.empty(5001, dtype=torch.int64, device="cuda")
+    total = C.c_int64()
+    call("pg_range", t.handle, q.data_ptr(), 5000, 0.05, 0, None, offs.data_ptr(), C.byref(total), None)
+    n = total.value
+    assert n > 5000
+    one = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    offs1 = torch.empty_like(offs)
+    call("pg_range", t.handle, q.data_ptr(), 5000, 0.05, n, one.data_ptr(), offs1.data_ptr(), C.byref(total), None)
+    two = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    call("pg_range_fill", t.handle, q.data_ptr(), 5000, 0.05, offs.data_ptr(), n, two.data_ptr(), None)
+    assert torch.equal(offs, offs1) and torch.equal(one, two)      # same rows, same order
+    # offsets of a smaller radius used with a larger one: rows overflow their
+    # offsets; the call reports it and writes nothing at or above capacity
+    small = torch.empty_like(offs)
+    call("pg_range", t.handle, q.data_ptr(), 5000, 0.02, 0, None, small.data_ptr(), C.byref(total), None)
+    ns = total.value
+    buf = torch.full((ns + 64,), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(PgError) as e:
+        call("pg_range_fill", t.handle, q.data_ptr(), 5000, 0.05, small.data_ptr(), ns, buf.data_ptr(), None)
+    assert e.value.status == PG_EINVAL
+    assert bool((buf[ns:] == -7).all())
+    # capacity below the last offset: reported, nothing written at or above it
+    with pytest.raises(PgError) as e:
+        call("pg_range_fill", t.handle, q.data_ptr(), 5000, 0.05, offs.data_ptr(), n - 10, two.data_ptr(), None)
+    assert e.value.status == PG_EINVAL
+    t.free()
