@@ -699,14 +699,14 @@ def run_ours(args):
 
 def extras_only(names):
     """Only the named other workloads (one JSON line), for profiling."""
-    import torch
-
-    from paper_2207_01834_gb300 import api
-
     only = [x for x in names.split(",") if x]
     unknown = [x for x in only if x not in EXTRAS]
     if unknown:
         raise SystemExit(f"unknown workloads {unknown}; choose from {', '.join(EXTRAS)}")
+    import torch
+
+    from paper_2207_01834_gb300 import api
+
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     print(json.dumps({"other_configs": other_configs(api, torch, dev, only=only)}), flush=True)
