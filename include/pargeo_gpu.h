@@ -360,7 +360,9 @@ PG_API pg_status pg_knn_backward_noalloc(const float *data, int64_t n, const flo
  * bounded, for its two trees).  The plan (layout, queue, a CUDA graph of the
  * launch sequence) is cached per (offsets, dim, k, leaf_size); each call
  * replays the graph on `stream` and synchronises once to read the wait
- * status.  Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT (a wait gave up).
+ * status.  Calls from several host threads run one at a time (the cached
+ * plans' buffers are shared).  Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA,
+ * PG_ETIMEOUT (a wait gave up).
  */
 PG_API pg_status pg_batched_chamfer(const float *a, const int64_t *a_off, const float *b,
                              const int64_t *b_off, int npairs, int dim, int k, int leaf_size,

@@ -433,11 +433,11 @@ pg_status make_plan(Plan &pl) {
     return PG_OK;
 }
 
+// The caller holds g_plans_mu until it is done with the plan's buffers.
 pg_status get_plan(const int64_t *a_off, const int64_t *b_off, int npairs, int dim, int k, int leaf, Plan **out) {
     std::vector<long long> key = {npairs, dim, k, leaf};
     for (int i = 0; i <= npairs; ++i) key.push_back(a_off[i]);
     for (int i = 0; i <= npairs; ++i) key.push_back(b_off[i]);
-    std::lock_guard<std::mutex> lk(g_plans_mu);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) { *out = it->second.get(); return PG_OK; }
     std::unique_ptr<Plan> pl(new Plan());
@@ -483,6 +483,11 @@ extern "C" pg_status pg_batched_chamfer(const float *a, const int64_t *a_off, co
     PG_TRY(check_offsets(b_off, npairs, "b_off"));
     if ((a_off[npairs] + b_off[npairs]) * (int64_t)k >= ((int64_t)1 << 31))
         return fail(PG_EINVAL, "pg_batched_chamfer: (|a| + |b|) * k must be < 2^31");
+    // A plan's argument block, loss and status buffers are shared by every
+    // call with its shapes, and the cache may drop plans: the lock is held
+    // until this call's stream has passed its last use of them (the status
+    // read below synchronises it), so concurrent calls run one at a time.
+    std::lock_guard<std::mutex> lk(g_plans_mu);
     Plan *pl = nullptr;
     PG_TRY(get_plan(a_off, b_off, npairs, dim, k, leaf_size, &pl));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
