@@ -69,6 +69,10 @@ def test_invalid_arguments_rejected_without_launch(lib):
     assert _status(lib, "pg_bdl_create", 0, 64, 16, None, C.byref(out)) == 1             # dim 0
     assert _status(lib, "pg_bdl_create", 3, 0, 16, None, C.byref(out)) == 1             # X = 0
     assert _status(lib, "pg_knn_backward", fake, 10, fake, 10, 3, 0, fake, fake, fake, fake, None) == 1  # k=0
+    total = C.c_int64()
+    assert _status(lib, "pg_range", None, fake, 10, C.c_float(0.1), 0, None, fake, C.byref(total), None) == 1
+    assert _status(lib, "pg_range_fill", None, fake, 10, C.c_float(0.1), fake, 10, fake, None) == 1  # NULL tree
+    assert _status(lib, "pg_knn_graph", None, 5, 0, None, C.byref(total), None) == 1                # NULL tree
     assert lib.pg_launch_count() == before
 
 
