@@ -126,3 +126,31 @@ def test_random_history_invariants_and_knn():
     a = oracle.knn(live_pts, q, 5, ids=ids)
     b = oracle.knn(everything, q, 5, live=alive)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_half_full_tree_stays_fewer_than_half_is_rebuilt():
+    """Erase_L gathers only trees left with FEWER than half their capacity
+    (Appendix A.3): slot 1 (capacity 2X) keeps X live points and stays; one
+    more erase leaves X - 1 and its points go back through Insert_L."""
+    X = 4
+    m = BDLModel(1, X)
+    pts = np.arange(2 * X, dtype=np.float32)[:, None]
+    m.insert(pts)
+    assert m.F == 0b10 and m.slot_sizes() == {1: 2 * X}
+    m.erase(pts[:X])
+    assert m.F == 0b10 and m.slot_sizes() == {1: X} and m.buffer == []
+    m.erase(pts[X:X + 1])
+    assert m.F == 0 and m.slot_sizes() == {} and len(m.buffer) == X - 1
+    m.check_invariants()
+
+
+def test_erase_reaches_the_buffer_tree():
+    X = 8
+    m = BDLModel(2, X)
+    pts = synth.uniform(3 * X + 3, 2, seed=7)           # 3 points end up in the buffer
+    ids = m.insert(pts)
+    assert sorted(m.buffer) == list(ids[-3:])
+    m.erase(pts[-2:])
+    assert sorted(m.buffer) == [ids[-3]]
+    assert set(m.live_ids()) == set(ids[:-2].tolist())
+    m.check_invariants()
