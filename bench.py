@@ -674,6 +674,10 @@ def run_ours(args):
     if rec is not None and "l2_sector_hit_pct" in rec:
         roofline["cache_hit_pct"] = {"l2": rec["l2_sector_hit_pct"], "l2_reads": rec["l2_read_sector_hit_pct"],
                                      "l1": rec["l1_sector_hit_pct"], "source": "ncu, profiles/"}
+    if rec is not None and "alu_pipe_pct" in rec:
+        # the unit that does bound the traversal: ALU pipe and issue slots
+        roofline["pipe_util_pct"] = {"alu": rec["alu_pipe_pct"], "issue": rec["issue_active_pct"],
+                                     "source": "ncu, profiles/"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
