@@ -76,6 +76,23 @@ def test_invalid_arguments_rejected_without_launch(lib):
     assert lib.pg_launch_count() == before
 
 
+def test_injected_allocation_failure_is_reported_before_any_cuda_call(lib):
+    """The allocation fault hook (host side): the next device allocation fails
+    with PG_ENOMEM, reported through the status and the error text; the tree
+    build's first allocation comes before any CUDA call, so no GPU is needed."""
+    out = C.c_void_p()
+    fake = C.c_void_p(0x1000)   # never dereferenced: the allocation fails first
+    before = lib.pg_launch_count()
+    assert lib.pg_debug_fail_alloc_after(1) == 0
+    try:
+        assert _status(lib, "pg_tree_build", fake, 10, 3, 16, None, C.byref(out)) == 2     # PG_ENOMEM
+        assert b"injected" in lib.pg_last_error()
+        assert out.value is None
+    finally:
+        lib.pg_debug_fail_alloc_after(0)
+    assert lib.pg_launch_count() == before
+
+
 def test_header_documents_every_entry_point():
     """Each declaration in the header is preceded by a comment."""
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
