@@ -713,6 +713,7 @@ def extras_only(names):
 
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
+    api.pg_knn_set_variant(3)   # as in the full run, which sets its traversal before these workloads
     print(json.dumps({"other_configs": other_configs(api, torch, dev, only=only)}), flush=True)
 
 
