@@ -102,3 +102,25 @@ def test_header_documents_every_entry_point():
             if m:
                 prev = "\n".join(lines[max(0, i - 30):i])
                 assert "*/" in prev, f"{m.group(1)} has no comment"
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_compiles_for_c_and_cxx_consumers(tmp_path, lang, std):
+    """A plain C or C++ program can include the header and link against the
+    library's symbols by name (syntax and type check with the host compiler)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("use.c" if lang == "c" else "use.cpp")
+    src.write_text('#include "pargeo_gpu.h"\n'
+                   "int use(const float *p, long long n) {\n"
+                   "    pg_tree *t = 0;\n"
+                   "    pg_status s = pg_tree_build(p, n, 3, 16, 0, &t);\n"
+                   "    if (s == PG_OK) s = pg_tree_free(t);\n"
+                   "    return (int)s;\n"
+                   "}\n")
+    subprocess.check_call([cc, "-fsyntax-only", std, "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src)])
+
