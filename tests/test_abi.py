@@ -124,3 +124,35 @@ def test_header_compiles_for_c_and_cxx_consumers(tmp_path, lang, std):
                    "}\n")
     subprocess.check_call([cc, "-fsyntax-only", std, "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src)])
 
+
+def test_plain_c_program_links_and_calls_the_library(lib, tmp_path):
+    """A C program linked against the shared library calls it through the C
+    ABI alone: version string, argument validation, thread-local error text
+    (no GPU work)."""
+    import shutil
+    import subprocess
+
+    from paper_2207_01834_gb300.build import LIB
+
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / "main.c"
+    src.write_text('#include <stdio.h>\n#include <string.h>\n#include "pargeo_gpu.h"\n'
+                   "int main(void) {\n"
+                   "    pg_tree *t = 0;\n"
+                   "    float p[3] = {0, 0, 0};\n"
+                   "    if (!strstr(pg_version(), \"sm_103a\")) return 2;\n"
+                   "    if (pg_tree_build(p, 1, 0, 16, 0, &t) != PG_EINVAL || t) return 3;\n"
+                   "    if (strlen(pg_last_error()) == 0) return 4;\n"
+                   "    puts(pg_last_error());\n"
+                   "    return 0;\n"
+                   "}\n")
+    exe = tmp_path / "main"
+    libdir = os.path.dirname(LIB)
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-L", libdir, "-lpargeo_gpu", "-Wl,-rpath," + libdir, "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "dim" in r.stdout
+
