@@ -156,3 +156,27 @@ def test_plain_c_program_links_and_calls_the_library(lib, tmp_path):
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert "dim" in r.stdout
 
+
+def test_error_text_is_per_thread(lib):
+    """pg_last_error is thread-local: two threads failing differently at the
+    same time each read their own message."""
+    import threading
+
+    fake = C.c_void_p(0x1000)
+    bad = []
+
+    def worker(dim, leaf, word):
+        out = C.c_void_p()
+        for _ in range(2000):
+            if lib.pg_tree_build(fake, 10, dim, leaf, None, C.byref(out)) != 1 or word not in lib.pg_last_error():
+                bad.append(word)
+                return
+
+    ts = [threading.Thread(target=worker, args=(0, 16, b"dim")),
+          threading.Thread(target=worker, args=(3, 0, b"leaf_size"))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert bad == []
+
