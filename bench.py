@@ -152,25 +152,50 @@ def traffic_record(kernel: str, sha: str, variant: int, leaf: int):
     return d
 
 
-def cpu_baseline(pts, k, budget_s=12.0):
-    """The oracle as it stands on a bounded sample of the queries."""
+PARITY_POOL = 16384   # rows of the timed output kept for the oracle comparison
+
+
+def parity_record(pts, rows, g_idx, g_dist, o_idx, o_dist):
+    """Compare the GPU's rows with the oracle's under the tests' rule (tie-
+    tolerant index sets, distances within 1e-5 relative)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from knn_compare import compare_knn
+
+    q = pts[rows]
+    try:
+        ties = compare_knn(g_idx, g_dist, o_idx, o_dist, pts, q)
+        return {"parity_rows": int(len(rows)), "mismatches": 0, "ties_resolved_otherwise": int(ties)}
+    except AssertionError:
+        bad = 0
+        for r in range(len(rows)):
+            try:
+                compare_knn(g_idx[r:r + 1], g_dist[r:r + 1], o_idx[r:r + 1], o_dist[r:r + 1], pts, q[r:r + 1])
+            except AssertionError:
+                bad += 1
+        return {"parity_rows": int(len(rows)), "mismatches": bad}
+
+
+def cpu_baseline(pts, k, pool, g_idx, g_dist, budget_s=12.0):
+    """The oracle as it stands on a bounded sample of the queries: the first
+    rows of `pool`, whose GPU answers from the timed run are g_idx / g_dist.
+    Returns the timing record and the parity record of those rows."""
     import oracle
 
     threads = oracle.default_threads()
     n = len(pts)
-    rng = np.random.default_rng(7)
-    probe = pts[rng.choice(n, size=min(n, max(threads, 16)), replace=False)]
+    probe = pts[pool[:max(threads, 16)]]
     t0 = time.perf_counter()
     oracle.knn(pts, probe, k, nthreads=threads)
     per_q = (time.perf_counter() - t0) / len(probe)
-    m = int(min(n, max(len(probe), budget_s / max(per_q, 1e-9))))
-    sample = pts[rng.choice(n, size=m, replace=False)]
+    m = int(min(len(pool), max(len(probe), budget_s / max(per_q, 1e-9))))
+    rows = pool[:m]
     t0 = time.perf_counter()
-    oracle.knn(pts, sample, k, nthreads=threads)
+    o_idx, o_dist = oracle.knn(pts, pts[rows], k, nthreads=threads)
     dt = time.perf_counter() - t0
-    return {"value": m / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{m} all-kNN queries (k={k}) against all {n} points, float64 brute force",
-            "extrapolated_full_run_s": n / (m / dt)}
+    rec = {"value": m / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{m} all-kNN queries (k={k}) against all {n} points, float64 brute force",
+           "extrapolated_full_run_s": n / (m / dt)}
+    return rec, parity_record(pts, rows, g_idx[:m], g_dist[:m], o_idx, o_dist)
 
 
 def batched_vs_plain(api, torch, dev, k: int, reps: int = 3):
@@ -359,9 +384,8 @@ def object_median(api, torch, dev, timed, out):
         ho["t"] = api.pg_tree_build_split(xo, 48, api.SPLIT_OBJECT)
 
     def qo():
-        api.pg_knn(ho["t"], None, 10)
+        api.pg_knn(ho["t"], None, 10, variant=3)
 
-    api.pg_knn_set_variant(3)
     obms = timed(bo)
     oqms = timed(qo)
     ho["t"].free()
@@ -384,7 +408,7 @@ def gmm_5d_7d(api, torch, dev, timed, out):
             h["t"] = api.pg_tree_build(pts, leaf_d)
 
         def qd():
-            api.pg_knn(h["t"], q, 16)
+            api.pg_knn(h["t"], q, 16, variant=var_d)
 
         bms = timed(bd)
         qms = timed(qd)
@@ -518,22 +542,19 @@ def run_ours(args):
         from paper_2207_01834_gb300 import autotune
         leaf, variant = autotune.best_config(x, K, leaves=(leaf,) if leaf > 0 else autotune.LEAF_CANDIDATES,
                                              variants=(variant,) if variant > 0 else autotune.VARIANT_CANDIDATES)
-    api.pg_knn_set_variant(variant)
     idx = torch.empty((n, K), dtype=torch.int32, device=dev)
     dst = torch.empty((n, K), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def step():
         t = api.pg_tree_build(x, leaf_size=leaf)
-        api.pg_knn(t, None, K, out_idx=idx, out_dist=dst)
+        api.pg_knn(t, None, K, out_idx=idx, out_dist=dst, variant=variant)
         t.free()
 
     for _ in range(args.warmup):
         step()
     barrier()
     launches0 = api.launch_count()
-    api.profile_enable(True)
-    api.profile_read("")  # clear
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()
@@ -542,13 +563,31 @@ def run_ours(args):
             step()
         ev1.record(stream)
         barrier()
-    api.profile_enable(False)
     launches = api.launch_count() - launches0
-    knn_ms, knn_launches = api.profile_read("knn_traverse")
-    api.profile_read("")
     total_ms, qps = combine_ranks(dist, dev, ev0.elapsed_time(ev1), n * args.steps, ws)
     ms_per_step = total_ms / args.steps
     value = qps / 1e6
+    # the timed run's own answers for a seeded pool of rows (checked against
+    # the oracle with the CPU baseline below)
+    pool = synth.pick_rows(n, min(n, PARITY_POOL), synth.BASE_SEED + 77)
+    rows_dev = torch.from_numpy(pool.astype(np.int64)).to(dev)
+    par_idx = idx[rows_dev].cpu().numpy()
+    par_dst = dst[rows_dev].cpu().numpy()
+
+    # a second pass of the same steps with the library's per-kernel event
+    # timers on (not the headline number): the traversal's average launch time
+    api.profile_enable(True)
+    api.profile_read("")  # clear
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(args.steps):
+        step()
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    api.profile_enable(False)
+    knn_ms, knn_launches = api.profile_read("knn_traverse")
+    api.profile_read("")
+    profiled_ms_per_step = pe0.elapsed_time(pe1) / args.steps
 
     # build and query separately (reported, not the headline)
     b_times, q_times = [], []
@@ -557,7 +596,7 @@ def run_ours(args):
         e0.record(stream)
         t = api.pg_tree_build(x, leaf_size=leaf)
         e1.record(stream)
-        api.pg_knn(t, None, K, out_idx=idx, out_dist=dst)
+        api.pg_knn(t, None, K, out_idx=idx, out_dist=dst, variant=variant)
         e2.record(stream)
         torch.cuda.synchronize()
         b_times.append(e0.elapsed_time(e1))
@@ -606,7 +645,7 @@ def run_ours(args):
             ev = torch.cuda.Event()
             ev.record(stream)
             built[b] = ev
-            api.pg_knn(t, None, K, out_idx=d_idx[b], out_dist=d_dst[b])
+            api.pg_knn(t, None, K, out_idx=d_idx[b], out_dist=d_dst[b], variant=variant)
             ready = torch.cuda.Event()
             ready.record(stream)
             down.wait_event(ready)
@@ -657,7 +696,7 @@ def run_ours(args):
         t = api.pg_tree_build(x, leaf_size=leaf)
         api.pg_knn_touch_read()
         api.pg_knn_touch_enable(True)
-        api.pg_knn(t, None, K, out_idx=idx, out_dist=dst)
+        api.pg_knn(t, None, K, out_idx=idx, out_dist=dst, variant=variant)
         api.pg_knn_touch_enable(False)
         nrec, nent = api.pg_knn_touch_read()
         t.free()
@@ -670,7 +709,10 @@ def run_ours(args):
                 "touched_bytes_per_launch": touched,
                 "touched_frac": None if touched is None else touched / (knn_avg_ms / 1e3) / 1e9 / peak,
                 "alg_bytes_per_launch": alg_bytes,
-                "avg_launch_ms": knn_avg_ms, "launches_timed": knn_launches, "source_sha": sha}
+                "avg_launch_ms": knn_avg_ms, "launches_timed": knn_launches,
+                "launch_ms_source": "library event timers around each traversal launch, in a second pass of the "
+                                    "same steps right after the timed one",
+                "profiled_pass_ms_per_step": profiled_ms_per_step, "source_sha": sha}
     if rec is not None and "l2_sector_hit_pct" in rec:
         roofline["cache_hit_pct"] = {"l2": rec["l2_sector_hit_pct"], "l2_reads": rec["l2_read_sector_hit_pct"],
                                      "l1": rec["l1_sector_hit_pct"], "source": "ncu, profiles/"}
@@ -694,7 +736,7 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         line["other_configs"] = other_configs(api, torch, dev)
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(pts, K)
+        line["cpu_baseline"], line["parity"] = cpu_baseline(pts, K, pool, par_idx, par_dst)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -713,7 +755,6 @@ def extras_only(names):
 
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
-    api.pg_knn_set_variant(3)   # as in the full run, which sets its traversal before these workloads
     print(json.dumps({"other_configs": other_configs(api, torch, dev, only=only)}), flush=True)
 
 

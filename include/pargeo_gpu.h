@@ -76,7 +76,9 @@ typedef struct pg_bdl pg_bdl;     /* one BDL-tree forest (opaque)               
  * spatial-median split, Section 6 "Construction"); a node with at most
  * leaf_size points, with all points equal, or at depth PG_DEPTH_CAP is a leaf.
  * n may be 0 (empty tree).  leaf_size in [1, PG_MAX_LEAF]; n < 2^31.
- * Synchronises with `stream` once per tree level (it reads level sizes).
+ * Synchronises with `stream` a few times per build (it reads the root box,
+ * the level loop's end flag once the expected depth is reached, the root
+ * record and it uploads the tree descriptor), never once per level.
  * On success *out receives a handle owned by the caller (free with
  * pg_tree_free).  Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA.
  */
@@ -97,6 +99,25 @@ PG_API pg_status pg_tree_build(const float *points, int64_t n, int dim, int leaf
 PG_API pg_status pg_tree_build_split(const float *points, int64_t n, int dim, int leaf_size, int split_rule,
                                      void *stream, pg_tree **out);
 
+/* Traversal kernels of the k-NN calls (paper App. A.1.3 searches every query
+ * independently; every variant returns the same exact answer, bit for bit,
+ * so the choice changes only speed):
+ *   PG_KNN_THREAD     one thread per query walks its own path;
+ *   PG_KNN_PACKET     the 32 queries of a warp, adjacent in tree order, share
+ *                     one walk and every lane scans every leaf any of them
+ *                     needs;
+ *   PG_KNN_POSTPONED  one thread per query with postponed leaves: lanes walk
+ *                     nodes until each holds a leaf, then scan their leaves
+ *                     together;
+ *   PG_KNN_AUTO       the calling thread's pg_knn_set_variant choice if set,
+ *                     else the tune table entry for the request's dimension
+ *                     class, k class and kind (all-kNN or separate queries)
+ *                     (pg_knn_tune_set), else PG_KNN_POSTPONED. */
+#define PG_KNN_AUTO 0
+#define PG_KNN_THREAD 1
+#define PG_KNN_PACKET 2
+#define PG_KNN_POSTPONED 3
+
 /*
  * Exact k-NN of m query points (device, m*dim float32) against the tree's
  * points (paper Appendix A.1.3, "Data-Parallel k-NN": every query searched
@@ -105,11 +126,19 @@ PG_API pg_status pg_tree_build_split(const float *points, int64_t n, int dim, in
  * tree's own points and m must equal the tree's n; row i of the output then
  * belongs to input point i (each point finds itself at distance 0).
  * out_idx (device, m*k int32) and out_dist (device, m*k float32).
- * k in [1, PG_MAX_K].  Stream-ordered, no synchronisation.
- * Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA.
+ * k in [1, PG_MAX_K].  The traversal is PG_KNN_AUTO's choice.
+ * Stream-ordered, no synchronisation.  Separate queries (m >= 4096) are first
+ * ordered by the leaf they fall in (scratch of 4 * m bytes), so that a warp's
+ * queries are neighbours.  Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA.
  */
 PG_API pg_status pg_knn(const pg_tree *tree, const float *queries, int64_t m, int k, int32_t *out_idx,
                  float *out_dist, void *stream);
+
+/* pg_knn with the traversal named per call (a PG_KNN_* value): two threads,
+ * or two trees, can use different variants at once.  Errors: as pg_knn, and
+ * PG_EINVAL for an unknown variant. */
+PG_API pg_status pg_knn_ex(const pg_tree *tree, const float *queries, int64_t m, int k, int variant,
+                           int32_t *out_idx, float *out_dist, void *stream);
 
 /* Release a tree.  Work that uses the tree must be ordered before this call on
  * the tree's build stream.  NULL is accepted. */
@@ -215,17 +244,25 @@ PG_API pg_status pg_range_fill(const pg_tree *tree, const float *queries, int64_
                                const int64_t *offsets, int64_t capacity, int32_t *out_idx, void *stream);
 
 /*
- * Traversal variant used by pg_knn and pg_bdl_knn for every later call in this
- * process (App. A.1.3 searches each query independently; every variant returns
- * that same exact answer): 1 = one thread per query walks its own path;
- * 2 = warp packets: the 32 queries of a warp, adjacent in tree order, share one
- * walk and every lane scans every leaf any of them needs; 3 = one thread per
- * query with postponed leaves: lanes walk nodes until each holds a leaf, then
- * scan their leaves together; 0 = automatic (currently 1).  Separate queries
- * (m >= 4096) are first reordered by the leaf they fall in, so that a warp's
- * queries are neighbours.  Errors: PG_EINVAL for other values.
+ * The calling thread's traversal override: every later PG_KNN_AUTO request of
+ * this thread (pg_knn, pg_bdl_knn, pg_knn_graph, and the *_ex calls given
+ * PG_KNN_AUTO) uses `variant`; PG_KNN_AUTO clears it.  Other threads are not
+ * affected.  Errors: PG_EINVAL for an unknown variant.
  */
 PG_API pg_status pg_knn_set_variant(int variant);
+
+/*
+ * Tune table of PG_KNN_AUTO (process-wide, safe to call from any thread):
+ * requests whose dimension class (dim 1-2, 3, ..., 8, 9-12, 13-16), k class
+ * (1, 2, 3-4, 5-8, 9-10, 11-16, 17-32, 33-64) and kind (all_knn != 0: the
+ * tree's own points; 0: separate queries) match use `variant`; PG_KNN_AUTO
+ * removes the entry.  An autotuner that timed the variants on its workload
+ * records its choice here.  pg_knn_tune_get returns the variant a
+ * PG_KNN_AUTO request of the calling thread resolves to.  Errors: PG_EINVAL
+ * for dim, k or variant out of range or a NULL output.
+ */
+PG_API pg_status pg_knn_tune_set(int dim, int k, int all_knn, int variant);
+PG_API pg_status pg_knn_tune_get(int dim, int k, int all_knn, int *variant);
 
 /*
  * Touched-bytes counters of the traversal (measurement only; no counterpart in
@@ -279,10 +316,14 @@ PG_API pg_status pg_bdl_erase(pg_bdl *bdl, const float *points, int64_t cnt);
  * Exact k-NN of m queries over the whole forest: one k-buffer per query is
  * carried across every non-empty tree (kNN_L), so the answer is the k-NN of
  * the live point set.  out_idx holds point ids.  Arguments as in pg_knn
- * (queries must not be NULL).
+ * (queries must not be NULL); the traversal is PG_KNN_AUTO's choice.
  */
 PG_API pg_status pg_bdl_knn(const pg_bdl *bdl, const float *queries, int64_t m, int k, int32_t *out_idx,
                      float *out_dist);
+
+/* pg_bdl_knn with the traversal named per call (a PG_KNN_* value). */
+PG_API pg_status pg_bdl_knn_ex(const pg_bdl *bdl, const float *queries, int64_t m, int k, int variant,
+                               int32_t *out_idx, float *out_dist);
 
 /* Number of live points. */
 PG_API pg_status pg_bdl_size(const pg_bdl *bdl, int64_t *live);
@@ -332,9 +373,13 @@ PG_API pg_status pg_knn_backward(const float *data, int64_t n, const float *quer
  * Limits: n <= 1,048,576 data points and m*k <= 1,048,576 (query, neighbour)
  * pairs; larger requests return PG_EINVAL and launch nothing.
  * All calls share the array: calls whose GPU work overlaps (for example on two
- * streams at once) race and must be serialised by the caller.  The first call
- * on a device looks up the array's device address with that device current;
- * make that first call before any stream capture.  Stream-ordered otherwise.
+ * streams at once) race and must be serialised by the caller.  Outside stream
+ * capture every call looks up the array's device address with the calling
+ * thread's device current; under capture the address found by the last
+ * uncaptured call on that device is reused, so make the first call on a
+ * device, and the first after a device reset, before any capture (a captured
+ * first call returns PG_EINVAL).  One context per device is assumed: the
+ * runtime's primary context.  Stream-ordered otherwise.
  */
 PG_API pg_status pg_knn_backward_noalloc(const float *data, int64_t n, const float *queries, int64_t m,
                                          int dim, int k, const int32_t *idx, const float *grad_dist,

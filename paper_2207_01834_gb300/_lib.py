@@ -15,6 +15,8 @@ from .build import LIB
 PG_OK, PG_EINVAL, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT, PG_EUNSUPPORTED = range(6)
 STATUS_NAMES = {0: "PG_OK", 1: "PG_EINVAL", 2: "PG_ENOMEM", 3: "PG_ECUDA", 4: "PG_ETIMEOUT",
                 5: "PG_EUNSUPPORTED"}
+KNN_AUTO, KNN_THREAD, KNN_PACKET, KNN_POSTPONED = 0, 1, 2, 3
+KNN_VARIANTS = (KNN_THREAD, KNN_PACKET, KNN_POSTPONED)
 MAX_DIM = 16
 MAX_K = 64
 MAX_LEAF = 256
@@ -43,6 +45,9 @@ SIGNATURES = {
     "pg_tree_build": (_S, [_P, _I64, _I, _I, _P, C.POINTER(_P)]),
     "pg_tree_build_split": (_S, [_P, _I64, _I, _I, _I, _P, C.POINTER(_P)]),
     "pg_knn": (_S, [_P, _P, _I64, _I, _P, _P, _P]),
+    "pg_knn_ex": (_S, [_P, _P, _I64, _I, _I, _P, _P, _P]),
+    "pg_knn_tune_set": (_S, [_I, _I, _I, _I]),
+    "pg_knn_tune_get": (_S, [_I, _I, _I, C.POINTER(_I)]),
     "pg_tree_free": (_S, [_P]),
     "pg_tree_info": (_S, [_P, C.POINTER(TreeInfo)]),
     "pg_tree_export": (_S, [_P, _P, _P, _P, _P]),
@@ -56,6 +61,7 @@ SIGNATURES = {
     "pg_bdl_insert": (_S, [_P, _P, _I64, _P]),
     "pg_bdl_erase": (_S, [_P, _P, _I64]),
     "pg_bdl_knn": (_S, [_P, _P, _I64, _I, _P, _P]),
+    "pg_bdl_knn_ex": (_S, [_P, _P, _I64, _I, _I, _P, _P]),
     "pg_bdl_size": (_S, [_P, C.POINTER(_I64)]),
     "pg_bdl_structure": (_S, [_P, C.POINTER(C.c_uint64), _P, C.POINTER(_I64), C.POINTER(_I64)]),
     "pg_bdl_slot_of": (_S, [_P, _P]),

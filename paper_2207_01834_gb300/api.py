@@ -13,10 +13,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import PgError, TreeInfo, call
+from ._lib import KNN_AUTO, KNN_PACKET, KNN_POSTPONED, KNN_THREAD, KNN_VARIANTS, PgError, TreeInfo, call
 
 __all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_tree_build_split", "pg_knn", "pg_tree_free", "pg_tree_info",
-           "pg_tree_export", "pg_knn_graph", "pg_range", "pg_knn_set_variant", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
+           "pg_tree_export", "pg_knn_graph", "pg_range", "pg_knn_set_variant", "pg_knn_tune_set", "pg_knn_tune_get", "KNN_AUTO", "KNN_THREAD", "KNN_PACKET",
+           "KNN_POSTPONED", "KNN_VARIANTS", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
            "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_knn_backward_noalloc",
            "pg_batched_chamfer",
            "pg_batched_chamfer_backward", "launch_count", "profile_enable", "profile_read", "version",
@@ -100,8 +101,19 @@ def pg_tree_build_split(points: torch.Tensor, leaf_size: int = 16, split_rule: i
     return Tree(out.value, (n, dim), pts.device)
 
 
-def pg_knn(tree: Tree, queries: torch.Tensor | None, k: int, out_idx=None, out_dist=None, stream=None):
-    """k-NN of `queries` (m, dim) or, with queries=None, all-kNN of the tree's points."""
+def _out(t, shape, dtype, dev, what):
+    if t is None:
+        return torch.empty(shape, dtype=dtype, device=dev)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or tuple(t.shape) != tuple(shape) \
+            or not t.is_contiguous() or t.device != dev:
+        raise ValueError(f"{what} must be a contiguous {dtype} CUDA tensor of shape {tuple(shape)} on {dev}")
+    return t
+
+
+def pg_knn(tree: Tree, queries: torch.Tensor | None, k: int, out_idx=None, out_dist=None, stream=None,
+           variant: int = KNN_AUTO):
+    """k-NN of `queries` (m, dim) or, with queries=None, all-kNN of the tree's points.
+    variant: KNN_AUTO (the library's choice) or a KNN_* traversal for this call."""
     if queries is None:
         m = tree.n
         qp = None
@@ -112,11 +124,11 @@ def pg_knn(tree: Tree, queries: torch.Tensor | None, k: int, out_idx=None, out_d
         m = queries.shape[0]
         qp = _ptr(queries)
     dev = tree.device
-    if out_idx is None:
-        out_idx = torch.empty((m, k), dtype=torch.int32, device=dev)
-    if out_dist is None:
-        out_dist = torch.empty((m, k), dtype=torch.float32, device=dev)
-    call("pg_knn", tree.handle, qp, m, k, _ptr(out_idx), _ptr(out_dist), _stream(stream))
+    if queries is not None and queries.device != dev:
+        raise ValueError("queries must be on the tree's device")
+    out_idx = _out(out_idx, (m, k), torch.int32, dev, "out_idx")
+    out_dist = _out(out_dist, (m, k), torch.float32, dev, "out_dist")
+    call("pg_knn_ex", tree.handle, qp, m, k, variant, _ptr(out_idx), _ptr(out_dist), _stream(stream))
     return out_idx, out_dist
 
 
@@ -177,8 +189,20 @@ def pg_range(tree: Tree, queries: torch.Tensor | None, radius: float, stream=Non
 
 
 def pg_knn_set_variant(variant: int) -> None:
-    """0 automatic, 1 thread per query, 2 warp packets, 3 postponed leaves (process-wide)."""
+    """This thread's traversal for KNN_AUTO requests (KNN_AUTO clears it)."""
     call("pg_knn_set_variant", variant)
+
+
+def pg_knn_tune_set(dim: int, k: int, all_knn: bool, variant: int) -> None:
+    """Record the traversal KNN_AUTO uses for (dim class, k class, kind), process-wide."""
+    call("pg_knn_tune_set", dim, k, 1 if all_knn else 0, variant)
+
+
+def pg_knn_tune_get(dim: int, k: int, all_knn: bool) -> int:
+    """The traversal a KNN_AUTO request of this thread resolves to."""
+    v = C.c_int()
+    call("pg_knn_tune_get", dim, k, 1 if all_knn else 0, C.byref(v))
+    return int(v.value)
 
 
 def pg_knn_touch_enable(on: bool = True) -> None:
@@ -227,8 +251,8 @@ class BDL:
     def erase(self, points: torch.Tensor) -> None:
         pg_bdl_erase(self, points)
 
-    def knn(self, queries: torch.Tensor, k: int):
-        return pg_bdl_knn(self, queries, k)
+    def knn(self, queries: torch.Tensor, k: int, variant: int = KNN_AUTO):
+        return pg_bdl_knn(self, queries, k, variant)
 
     def size(self) -> int:
         return pg_bdl_size(self)
@@ -257,12 +281,14 @@ def pg_bdl_erase(bdl: BDL, points: torch.Tensor) -> None:
     call("pg_bdl_erase", bdl.handle, _ptr(pts) if pts.shape[0] else None, pts.shape[0])
 
 
-def pg_bdl_knn(bdl: BDL, queries: torch.Tensor, k: int):
+def pg_bdl_knn(bdl: BDL, queries: torch.Tensor, k: int, variant: int = KNN_AUTO):
     q = _dev(queries, torch.float32, "queries", 2)
+    if q.shape[1] != bdl.dim:
+        raise ValueError("queries have the wrong dimension")
     m = q.shape[0]
     oi = torch.empty((m, k), dtype=torch.int32, device=q.device)
     od = torch.empty((m, k), dtype=torch.float32, device=q.device)
-    call("pg_bdl_knn", bdl.handle, _ptr(q) if m else None, m, k, _ptr(oi), _ptr(od))
+    call("pg_bdl_knn_ex", bdl.handle, _ptr(q) if m else None, m, k, variant, _ptr(oi), _ptr(od))
     return oi, od
 
 
@@ -293,14 +319,54 @@ def pg_bdl_free(bdl: BDL) -> None:
 
 
 # ---------------------------------------------------------------- backward
-def pg_knn_backward(data: torch.Tensor, queries: torch.Tensor, idx: torch.Tensor, grad_dist: torch.Tensor,
-                    need_queries: bool = True, need_data: bool = True, stream=None):
-    data = _dev(data, torch.float32, "data", 2)
-    queries = _dev(queries, torch.float32, "queries", 2)
-    idx = _dev(idx, torch.int32, "idx", 2)
-    grad_dist = _dev(grad_dist, torch.float32, "grad_dist", 2)
+def _backward_inputs(data, queries, idx, grad_dist):
+    """Checked (data, queries, idx, grad_dist, n, m, dim, k): float32/int32 CUDA
+    tensors on one device, queries (m, dim) matching data (n, dim), grad_dist
+    of idx's shape (m, k).  Types and shapes are checked before devices, so a
+    malformed call fails the same way on any machine, before any launch."""
+    spec = ((data, torch.float32, "data"), (queries, torch.float32, "queries"), (idx, torch.int32, "idx"),
+            (grad_dist, torch.float32, "grad_dist"))
+    for t, dtype, what in spec:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{what} must be a torch.Tensor")
+        if t.dtype != dtype:
+            raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+        if t.dim() != 2:
+            raise ValueError(f"{what} must have 2 dimensions")
     n, dim = data.shape
     m, k = idx.shape
+    if tuple(queries.shape) != (m, dim):
+        raise ValueError(f"queries must have shape ({m}, {dim}) to match idx and data, got {tuple(queries.shape)}")
+    if tuple(grad_dist.shape) != (m, k):
+        raise ValueError(f"grad_dist must have idx's shape ({m}, {k}), got {tuple(grad_dist.shape)}")
+    data = _dev(data, torch.float32, "data", 2)
+    for t, what in ((queries, "queries"), (idx, "idx"), (grad_dist, "grad_dist")):
+        if not t.is_cuda or t.device != data.device:
+            raise ValueError(f"{what} must be a CUDA tensor on data's device {data.device}")
+    return data, queries.contiguous(), idx.contiguous(), grad_dist.contiguous(), n, m, dim, k
+
+
+def _grad_out(t, shape, dev, what):
+    """A caller-provided gradient output: None, or a contiguous float32 CUDA
+    tensor of exactly `shape` on `dev` (never copied: the kernels write it)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what} must be a torch.Tensor or None")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{what} must be torch.float32, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if not t.is_cuda or t.device != dev:
+        raise ValueError(f"{what} must be a CUDA tensor on {dev}")
+    return t
+
+
+def pg_knn_backward(data: torch.Tensor, queries: torch.Tensor, idx: torch.Tensor, grad_dist: torch.Tensor,
+                    need_queries: bool = True, need_data: bool = True, stream=None):
+    data, queries, idx, grad_dist, n, m, dim, k = _backward_inputs(data, queries, idx, grad_dist)
     gq = torch.empty((m, dim), dtype=torch.float32, device=data.device) if need_queries else None
     gp = torch.empty((n, dim), dtype=torch.float32, device=data.device) if need_data else None
     call("pg_knn_backward", _ptr(data) if n else None, n, _ptr(queries) if m else None, m, dim, k,
@@ -310,19 +376,18 @@ def pg_knn_backward(data: torch.Tensor, queries: torch.Tensor, idx: torch.Tensor
 
 
 def pg_knn_backward_noalloc(data: torch.Tensor, queries: torch.Tensor, idx: torch.Tensor,
-                            grad_dist: torch.Tensor, grad_queries: torch.Tensor, grad_data: torch.Tensor,
-                            stream=None):
-    """pg_knn_backward into caller-provided outputs, using only the library's
-    fixed device scratch (no allocation by the library)."""
-    data = _dev(data, torch.float32, "data", 2)
-    queries = _dev(queries, torch.float32, "queries", 2)
-    idx = _dev(idx, torch.int32, "idx", 2)
-    grad_dist = _dev(grad_dist, torch.float32, "grad_dist", 2)
-    n, dim = data.shape
-    m, k = idx.shape
+                            grad_dist: torch.Tensor, grad_queries: torch.Tensor | None,
+                            grad_data: torch.Tensor | None, stream=None):
+    """pg_knn_backward into caller-provided outputs (grad_queries (m, dim),
+    grad_data (n, dim), float32, contiguous, on data's device; either may be
+    None), using only the library's fixed device scratch: the library
+    allocates nothing."""
+    data, queries, idx, grad_dist, n, m, dim, k = _backward_inputs(data, queries, idx, grad_dist)
+    gq = _grad_out(grad_queries, (m, dim), data.device, "grad_queries")
+    gp = _grad_out(grad_data, (n, dim), data.device, "grad_data")
     call("pg_knn_backward_noalloc", _ptr(data) if n else None, n, _ptr(queries) if m else None, m, dim, k,
-         _ptr(idx) if m else None, _ptr(grad_dist) if m else None, _ptr(grad_queries), _ptr(grad_data),
-         _stream(stream))
+         _ptr(idx) if m else None, _ptr(grad_dist) if m else None, _ptr(gq) if gq is not None and m else None,
+         _ptr(gp) if gp is not None and n else None, _stream(stream))
     return grad_queries, grad_data
 
 

@@ -46,20 +46,27 @@ pg_status pg_tree_build_split(const float *points, int64_t n, int dim, int leaf_
 
 pg_status pg_knn(const pg_tree *tree, const float *queries, int64_t m, int k, int32_t *out_idx, float *out_dist,
                  void *stream) {
+    return pg_knn_ex(tree, queries, m, k, PG_KNN_AUTO, out_idx, out_dist, stream);
+}
+
+pg_status pg_knn_ex(const pg_tree *tree, const float *queries, int64_t m, int k, int variant, int32_t *out_idx,
+                    float *out_dist, void *stream) {
     if (!tree) return fail(PG_EINVAL, "pg_knn: tree is NULL");
     if (k < 1 || k > PG_MAX_K) return fail(PG_EINVAL, "pg_knn: k must be in [1, 64]");
     if (m < 0 || m >= (int64_t)1 << 31) return fail(PG_EINVAL, "pg_knn: m must be in [0, 2^31)");
     if (!queries && m != tree->n) return fail(PG_EINVAL, "pg_knn: all-kNN (queries == NULL) needs m == n");
     if (m > 0 && (!out_idx || !out_dist)) return fail(PG_EINVAL, "pg_knn: output pointer is NULL");
+    if (!valid_variant(variant)) return fail(PG_EINVAL, "pg_knn: unknown traversal variant");
     if (m == 0) return PG_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (tree->n == 0) {
         // Nothing to find: every slot is padding.
-        return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, nullptr, m, tree->dim, k, out_idx, out_dist, s);
+        return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, nullptr, m, tree->dim, k, out_idx, out_dist,
+                          variant, s);
     }
     if (!queries)   // all-kNN: bucket order is already tree order
         return knn_launch(tree->desc, 1, tree->dc, nullptr, tree->bucket, nullptr, m, tree->dim, k, out_idx,
-                          out_dist, s);
+                          out_dist, variant, s);
     Scratch ord;
     const bool sorted = m >= kOrderMinQueries;
     if (sorted) {
@@ -67,7 +74,7 @@ pg_status pg_knn(const pg_tree *tree, const float *queries, int64_t m, int k, in
         PG_TRY(query_order(tree, queries, m, tree->dim, ord.as<int32_t>(), s));
     }
     return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr, m, tree->dim,
-                      k, out_idx, out_dist, s);
+                      k, out_idx, out_dist, variant, s);
 }
 
 pg_status pg_tree_free(pg_tree *tree) {

@@ -193,7 +193,8 @@ extern "C" pg_status pg_knn_backward(const float *data, int64_t n, const float *
                                      float *grad_data, void *stream) {
     if (k < 1 || k > PG_MAX_K) return fail(PG_EINVAL, "pg_knn_backward: k must be in [1, 64]");
     if (dim < 1 || dim > PG_MAX_DIM) return fail(PG_EINVAL, "pg_knn_backward: dim must be in [1, 16]");
-    if (n < 0 || m < 0 || n >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "pg_knn_backward: bad n or m");
+    if (n < 0 || m < 0 || n >= ((int64_t)1 << 31) || m >= ((int64_t)1 << 31))
+        return fail(PG_EINVAL, "pg_knn_backward: n and m must be in [0, 2^31)");
     if (m * (int64_t)k >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "pg_knn_backward: m*k must be < 2^31");
     if (m > 0 && (!queries || !idx || !grad_dist)) return fail(PG_EINVAL, "pg_knn_backward: NULL input");
     if (n > 0 && !data && (grad_data || (m > 0 && grad_queries))) return fail(PG_EINVAL, "pg_knn_backward: NULL data");

@@ -460,7 +460,13 @@ pg_status pg_bdl_erase(pg_bdl *b, const float *pts, int64_t cnt) {
 }
 
 pg_status pg_bdl_knn(const pg_bdl *b, const float *queries, int64_t m, int k, int32_t *out_idx, float *out_dist) {
+    return pg_bdl_knn_ex(b, queries, m, k, PG_KNN_AUTO, out_idx, out_dist);
+}
+
+pg_status pg_bdl_knn_ex(const pg_bdl *b, const float *queries, int64_t m, int k, int variant, int32_t *out_idx,
+                        float *out_dist) {
     if (!b) return fail(PG_EINVAL, "pg_bdl_knn: forest is NULL");
+    if (!valid_variant(variant)) return fail(PG_EINVAL, "pg_bdl_knn: unknown traversal variant");
     if (k < 1 || k > PG_MAX_K) return fail(PG_EINVAL, "pg_bdl_knn: k must be in [1, 64]");
     if (m < 0 || m >= ((int64_t)1 << 31)) return fail(PG_EINVAL, "pg_bdl_knn: m must be in [0, 2^31)");
     if (m > 0 && (!queries || !out_idx || !out_dist)) return fail(PG_EINVAL, "pg_bdl_knn: NULL pointer");
@@ -477,7 +483,7 @@ pg_status pg_bdl_knn(const pg_bdl *b, const float *queries, int64_t m, int k, in
         PG_TRY(query_order(big, queries, m, b->dim, ord.as<int32_t>(), b->s));
     }
     return knn_launch(b->forest, b->forest_n, b->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr, m, b->dim,
-                      k, out_idx, out_dist, b->s);
+                      k, out_idx, out_dist, variant, b->s);
 }
 
 pg_status pg_bdl_size(const pg_bdl *b, int64_t *live) {

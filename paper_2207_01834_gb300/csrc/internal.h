@@ -101,12 +101,16 @@ TreeDesc tree_desc(const pg_tree *t);
 // is the entry's id; otherwise queries are row-major m*dim floats.
 // order (may be NULL): processing order of the queries (a permutation of
 // 0..m-1 that puts queries of the same leaf next to each other).
+// variant: a PG_KNN_* traversal, or PG_KNN_AUTO for the automatic choice.
 pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
                      const float4 *self_bucket, const int32_t *order, int64_t m, int dim, int k,
-                     int32_t *out_idx, float *out_dist, cudaStream_t s);
+                     int32_t *out_idx, float *out_dist, int variant, cudaStream_t s);
 int k_class(int k);
-void set_knn_variant(int v);
-int knn_variant();
+bool valid_variant(int v);
+// The variant PG_KNN_AUTO resolves to for this thread and request.
+int resolve_variant(int requested, int dc, int k, bool self);
+// Internal launch code of the counting instance of the postponed-leaf kernel.
+constexpr int kKnnCountingInstance = 100;
 
 // ---- order.cu
 // Queries sorted by the leaf of `t` they fall in (stable); order gets m ints.

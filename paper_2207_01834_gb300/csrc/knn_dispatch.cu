@@ -1,4 +1,14 @@
 // Chooses the traversal kernel instance for a (dimension class, k) request.
+//
+// Every traversal variant returns the same exact answer (paper App. A.1.3:
+// each query is searched independently), so the choice only changes speed.
+// A call names its variant, or asks for the automatic one (PG_KNN_AUTO):
+// then the calling thread's override (pg_knn_set_variant) applies if set,
+// else the tune table entry for (dimension class, k class, all-kNN or
+// separate queries) that an autotuner recorded (pg_knn_tune_set), else the
+// built-in default.
+#include <atomic>
+
 #include "internal.h"
 
 namespace pg {
@@ -21,25 +31,60 @@ int k_class(int k) {
     return 64;
 }
 
-static int g_variant = 0;   // 0 automatic, 1 thread per query, 2 warp packets, 3 postponed leaves
-static bool g_touch = false;                   // count touched records / entries (postponed leaves)
-static unsigned long long *g_touch_dev = nullptr;   // [node records, bucket entries] (one device)
+namespace {
 
-void set_knn_variant(int v) { g_variant = v; }
-// automatic: thread per query (measured faster on 3D all-kNN so far)
-int knn_variant() { return g_variant == 0 ? 1 : g_variant; }
+constexpr int kDcSlots = 9;   // dimension classes 2, 3, 4, 5, 6, 7, 8, 12, 16
+constexpr int kKSlots = 8;    // k classes 1, 2, 4, 8, 10, 16, 32, 64
+
+int dc_slot(int dc) {
+    if (dc <= 8) return dc < 2 ? 0 : dc - 2;
+    return dc <= 12 ? 7 : 8;
+}
+int k_slot(int k) {
+    switch (k_class(k)) {
+        case 1: return 0;
+        case 2: return 1;
+        case 4: return 2;
+        case 8: return 3;
+        case 10: return 4;
+        case 16: return 5;
+        case 32: return 6;
+        default: return 7;
+    }
+}
+
+thread_local int t_override = 0;                      // pg_knn_set_variant of this thread
+std::atomic<int> g_tune[kDcSlots][kKSlots][2];         // 0: no entry (zero-initialised)
+std::atomic<bool> g_touch{false};                      // count touched records / entries
+unsigned long long *g_touch_dev = nullptr;             // [node records, bucket entries] (one device)
+
+// Built-in choice when nothing else is set: the postponed-leaf traversal,
+// the fastest measured variant on 3D all-kNN and on separate queries.
+int default_variant(int /*dc*/, int /*k*/, bool /*self*/) { return PG_KNN_POSTPONED; }
+
+}  // namespace
+
+bool valid_variant(int v) { return v >= PG_KNN_AUTO && v <= PG_KNN_POSTPONED; }
+
+int resolve_variant(int requested, int dc, int k, bool self) {
+    if (requested != PG_KNN_AUTO) return requested;
+    if (t_override != PG_KNN_AUTO) return t_override;
+    const int v = g_tune[dc_slot(dc)][k_slot(k)][self ? 1 : 0].load(std::memory_order_relaxed);
+    return v != PG_KNN_AUTO ? v : default_variant(dc, k, self);
+}
 
 pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
                      const float4 *self_bucket, const int32_t *order, int64_t m, int dim, int k, int32_t *out_idx,
-                     float *out_dist, cudaStream_t s) {
+                     float *out_dist, int requested, cudaStream_t s) {
     if (m == 0) return PG_OK;
-    int variant = knn_variant();
-    if (g_touch && variant == 3) {
+    if (!valid_variant(requested)) return fail(PG_EINVAL, "k-NN: unknown traversal variant");
+    int variant = resolve_variant(requested, dc, k, self_bucket != nullptr);
+    if (g_touch.load() && variant == PG_KNN_POSTPONED) {
         if (!g_touch_dev) {
             PG_CUDA(cudaMalloc(&g_touch_dev, 2 * sizeof(unsigned long long)));
             PG_CUDA(cudaMemset(g_touch_dev, 0, 2 * sizeof(unsigned long long)));
         }
-        variant = 4;   // the counting instance of the same traversal
+        variant = kKnnCountingInstance;   // the counting instance of the same traversal
     }
     unsigned long long *touch = g_touch_dev;
     switch (dc) {
@@ -59,7 +104,7 @@ pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float 
 }  // namespace pg
 
 extern "C" pg_status pg_knn_touch_enable(int on) {
-    pg::g_touch = on != 0;
+    pg::g_touch.store(on != 0);
     return PG_OK;
 }
 
@@ -77,7 +122,23 @@ extern "C" pg_status pg_knn_touch_read(int64_t *node_records, int64_t *bucket_en
 }
 
 extern "C" pg_status pg_knn_set_variant(int variant) {
-    if (variant < 0 || variant > 3) return pg::fail(PG_EINVAL, "pg_knn_set_variant: variant must be 0..3");
-    pg::set_knn_variant(variant);
+    if (!pg::valid_variant(variant)) return pg::fail(PG_EINVAL, "pg_knn_set_variant: unknown traversal variant");
+    pg::t_override = variant;
+    return PG_OK;
+}
+
+extern "C" pg_status pg_knn_tune_set(int dim, int k, int all_knn, int variant) {
+    if (dim < 1 || dim > PG_MAX_DIM) return pg::fail(PG_EINVAL, "pg_knn_tune_set: dim must be in [1, 16]");
+    if (k < 1 || k > PG_MAX_K) return pg::fail(PG_EINVAL, "pg_knn_tune_set: k must be in [1, 64]");
+    if (!pg::valid_variant(variant)) return pg::fail(PG_EINVAL, "pg_knn_tune_set: unknown traversal variant");
+    pg::g_tune[pg::dc_slot(pg::dim_class(dim))][pg::k_slot(k)][all_knn ? 1 : 0].store(variant);
+    return PG_OK;
+}
+
+extern "C" pg_status pg_knn_tune_get(int dim, int k, int all_knn, int *variant) {
+    if (!variant) return pg::fail(PG_EINVAL, "pg_knn_tune_get: variant is NULL");
+    if (dim < 1 || dim > PG_MAX_DIM) return pg::fail(PG_EINVAL, "pg_knn_tune_get: dim must be in [1, 16]");
+    if (k < 1 || k > PG_MAX_K) return pg::fail(PG_EINVAL, "pg_knn_tune_get: k must be in [1, 64]");
+    *variant = pg::resolve_variant(PG_KNN_AUTO, pg::dim_class(dim), k, all_knn != 0);
     return PG_OK;
 }

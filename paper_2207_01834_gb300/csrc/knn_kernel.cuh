@@ -677,17 +677,18 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
 }  // namespace pg
 
 // Host launcher for one dimension class: picks the list capacity KC >= k and
-// the traversal variant (1 = thread per query, otherwise warp packets).
+// the traversal kernel for the resolved variant (PG_KNN_THREAD,
+// PG_KNN_POSTPONED, the counting instance, else warp packets).
 #define PG_KNN_CASE(DCN, KCN)                                                                              \
     case KCN:                                                                                              \
-        if (variant == 1)                                                                                  \
+        if (variant == PG_KNN_THREAD)                                                                      \
             k_knn<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(trees, ntrees, queries,      \
                                                                                self_bucket, m, dim, k,     \
                                                                                out_idx, out_dist);         \
-        else if (variant == 3)                                                                             \
+        else if (variant == PG_KNN_POSTPONED)                                                              \
             k_knn_ww<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(                         \
                 trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist);                 \
-        else if (variant == 4)                                                                             \
+        else if (variant == kKnnCountingInstance)                                                          \
             k_knn_ww<DCN, KCN, true><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(                   \
                 trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, touch);          \
         else                                                                                               \

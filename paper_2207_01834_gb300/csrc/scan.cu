@@ -2,6 +2,7 @@
 // down-sweep).  Used by the tree builder (stable partition offsets, segment
 // numbering) and by stream compactions.
 #include "internal.h"
+#include "sort.h"
 
 namespace pg {
 
@@ -10,6 +11,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kItems = 16;
 constexpr int kTile = kThreads * kItems;
+static_assert(kTile == kScanTileItems, "scan tile published in sort.h");
 
 __device__ __forceinline__ int warp_incl_scan(int x) {
     const int lane = threadIdx.x & 31;
@@ -123,7 +125,7 @@ pg_status exclusive_scan(const int *in, int *out, int64_t n, cudaStream_t s) {
 
 // Same scan with caller-provided partial-sum workspace (scan_ws_words(n) ints):
 // allocates nothing.
-int64_t scan_ws_words(int64_t n) { return n <= 0 ? 1 : (int64_t)ceil_div_i(n, kTile) + 1; }
+int64_t scan_ws_words(int64_t n) { return scan_ws_words_ce(n); }
 
 pg_status exclusive_scan_ws(const int *in, int *out, int64_t n, int *ws, cudaStream_t s) {
     if (n <= 0) {

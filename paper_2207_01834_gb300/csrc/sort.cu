@@ -18,6 +18,7 @@ constexpr int kRounds = 8;                    // items per thread
 constexpr int kTile = kThreads * kRounds;     // 2048 items per tile
 constexpr int kRadix = 256;
 static_assert(kThreads == kRadix, "one thread per digit in the scatter's tile scan");
+static_assert(kTile == kRadixTileItems && kRadix == kRadixDigits, "tile constants published in sort.h");
 
 __global__ void __launch_bounds__(kThreads) k_rs_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
                                                       int ntiles, int *__restrict__ ghist) {
@@ -142,10 +143,8 @@ pg_status radix_sort_pairs(uint32_t *keys, uint32_t *vals, bool iota_vals, uint3
     return PG_OK;
 }
 
-int64_t radix_ws_words(int64_t n) {
-    const int64_t cells = (int64_t)kRadix * (n > 0 ? ceil_div_i(n, kTile) : 1);
-    return 2 * cells + 1 + scan_ws_words(cells);
-}
+// hist (cells) + offsets (cells + 1) + the offsets scan's partials
+int64_t radix_ws_words(int64_t n) { return radix_ws_words_ce(n); }
 
 pg_status radix_sort_pairs_ws(uint32_t *keys, uint32_t *vals, bool iota_vals, uint32_t *tk, uint32_t *tv,
                               int64_t n, int bits, int *ws, cudaStream_t s, uint32_t **out_keys,

@@ -5,6 +5,20 @@
 
 namespace pg {
 
+// Tile sizes of the radix sort (items per tile, digits per pass) and of the
+// device-wide scan (items per tile).  Workspace sizes follow from them; a
+// caller that reserves workspace at compile time sizes it with the constexpr
+// functions below, so a tile change cannot leave a reserve too small.
+constexpr int kRadixTileItems = 2048;
+constexpr int kRadixDigits = 256;
+constexpr int kScanTileItems = 4096;
+
+constexpr int64_t scan_ws_words_ce(int64_t n) { return n <= 0 ? 1 : (n + kScanTileItems - 1) / kScanTileItems + 1; }
+constexpr int64_t radix_ws_words_ce(int64_t n) {
+    return 2 * ((int64_t)kRadixDigits * (n > 0 ? (n + kRadixTileItems - 1) / kRadixTileItems : 1)) + 1 +
+           scan_ws_words_ce((int64_t)kRadixDigits * (n > 0 ? (n + kRadixTileItems - 1) / kRadixTileItems : 1));
+}
+
 // Sorts n pairs by the low `bits` bits of the key, stably.  keys/vals hold the
 // input (vals is ignored and the item index used instead when iota_vals);
 // tk/tv are temporaries of n entries.  The sorted arrays end in whichever pair

@@ -1,6 +1,7 @@
 """The autotuner's host logic on the CPU, with the timing call replaced: it
-picks the fastest (leaf size, variant), leaves that variant set, caches the
-choice per (GPU, workload shape) and reuses it without timing again."""
+picks the fastest (leaf size, traversal), records the traversal in the
+library's tune table (never in a process-wide override), caches the choice per
+(GPU, workload shape) and reuses it without timing again."""
 from __future__ import annotations
 
 import numpy as np
@@ -13,14 +14,15 @@ torch = pytest.importorskip("torch")
 def tuner(monkeypatch, tmp_path):
     from paper_2207_01834_gb300 import autotune
 
-    state = {"variant": None, "timed": []}
+    state = {"timed": [], "tuned": [], "override": []}
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
     monkeypatch.setattr(autotune.torch.cuda, "get_device_name", lambda *a: "GB300-test")
-    monkeypatch.setattr(autotune.api, "pg_knn_set_variant", lambda v: state.__setitem__("variant", v))
+    monkeypatch.setattr(autotune.api, "pg_knn_tune_set", lambda *a: state["tuned"].append(a))
+    monkeypatch.setattr(autotune.api, "pg_knn_set_variant", lambda v: state["override"].append(v))
 
-    def fake_time(x, queries, k, leaf, reps=2):
-        state["timed"].append((leaf, state["variant"]))
-        return abs(leaf - 32) + (0.5 if state["variant"] != 3 else 0.0)   # fastest: leaf 32, variant 3
+    def fake_time(x, queries, k, leaf, variant, reps=2):
+        state["timed"].append((leaf, variant))
+        return abs(leaf - 32) + (0.5 if variant != 3 else 0.0)   # fastest: leaf 32, variant 3
 
     monkeypatch.setattr(autotune, "_time_leaf", fake_time)
     return autotune, state
@@ -30,12 +32,13 @@ def test_picks_the_fastest_and_caches(tuner):
     autotune, state = tuner
     x = torch.from_numpy(np.zeros((5000, 3), np.float32))
     assert autotune.best_config(x, 10) == (32, 3)
-    assert state["variant"] == 3
+    assert state["tuned"] == [(3, 10, True, 3)]
     assert len(state["timed"]) == len(autotune.LEAF_CANDIDATES) * len(autotune.VARIANT_CANDIDATES)
+    assert set(v for _, v in state["timed"]) == set(autotune.VARIANT_CANDIDATES)
     state["timed"].clear()
-    state["variant"] = None
-    assert autotune.best_config(x, 10) == (32, 3)          # from the cache
-    assert state["timed"] == [] and state["variant"] == 3
+    assert autotune.best_config(x, 10, queries=None) == (32, 3)          # from the cache
+    assert state["timed"] == [] and state["tuned"][-1] == (3, 10, True, 3)
+    assert state["override"] == []                                       # no process-wide side effect
 
 
 def test_cache_key_separates_workloads(tuner):
@@ -45,7 +48,26 @@ def test_cache_key_separates_workloads(tuner):
     n_first = len(state["timed"])
     autotune.best_config(x, 16)                             # another k: timed again
     autotune.best_config(x, 10, queries=x)                  # separate queries: timed again
+    assert state["tuned"][-1] == (3, 10, False, 3)
     autotune.best_config(torch.from_numpy(np.zeros((70000, 3), np.float32)), 10)   # another size class
     assert len(state["timed"]) == 4 * n_first
     assert autotune.best_leaf(x, 10) == 32                  # cached
     assert len(state["timed"]) == 4 * n_first
+
+
+def test_batched_leaf_picks_fastest_and_caches(tuner, monkeypatch):
+    autotune, state = tuner
+    timed = []
+
+    def fake_time(a, a_off, b, b_off, k, leaf, reps=2):
+        timed.append(leaf)
+        return abs(leaf - 12) + 1.0
+
+    monkeypatch.setattr(autotune, "_time_batched", fake_time)
+    a = torch.zeros((300, 3))
+    off = np.array([0, 100, 300])
+    assert autotune.best_batched_leaf(a, off, a, off, 8) == 12
+    assert sorted(timed) == sorted(autotune.BATCHED_LEAF_CANDIDATES)
+    timed.clear()
+    assert autotune.best_batched_leaf(a, off, a, off, 8) == 12
+    assert timed == []

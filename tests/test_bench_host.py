@@ -70,8 +70,8 @@ def _standins(monkeypatch):
     torch = types.SimpleNamespace(from_numpy=_Arr, cuda=cuda, cat=lambda xs: _Arr(np.concatenate([x.a for x in xs])))
     api = types.SimpleNamespace(
         pg_tree_build=lambda x, leaf: _Tree(), pg_tree_build_split=lambda x, leaf, rule: _Tree(), SPLIT_OBJECT=1,
-        pg_knn=lambda t, q, k: None, pg_knn_graph=lambda t, k: _Arr(np.zeros((5, 2))),
-        pg_range=lambda t, q, r: (_Arr(np.zeros(7)), _Arr(np.zeros(3))), pg_knn_set_variant=lambda v: None,
+        pg_knn=lambda t, q, k, **kw: None, pg_knn_graph=lambda t, k: _Arr(np.zeros((5, 2))),
+        pg_range=lambda t, q, r: (_Arr(np.zeros(7)), _Arr(np.zeros(3))),
         BDL=_Forest)
     monkeypatch.setattr(autotune, "best_config", lambda pts, k, queries=None: (32, 3))
     return api, torch

@@ -25,6 +25,7 @@ def api():
 
 @pytest.fixture(params=[1, 2, 3], ids=["thread", "packet", "postponed"])
 def variant(api, request):
+    """This thread's traversal override for the test's PG_KNN_AUTO calls."""
     api.pg_knn_set_variant(request.param)
     yield request.param
     api.pg_knn_set_variant(0)
@@ -245,9 +246,22 @@ def _sample_rows(m, count, seed):
     return np.sort(synth.pick_rows(m, min(count, m), seed))
 
 
+def _check_all_knn_rows(idx, dist, n):
+    """Properties every all-kNN row must have, checked on the device for all
+    rows: ascending distances, the point itself first at distance 0 (uniform
+    float32 points are distinct), indices in range and distinct."""
+    assert torch.all(dist[:, 1:] >= dist[:, :-1])
+    assert torch.all(dist[:, 0] == 0)
+    assert torch.equal(idx[:, 0], torch.arange(n, dtype=torch.int32, device=idx.device))
+    assert torch.all((idx >= 0) & (idx < n))
+    srt = torch.sort(idx, dim=1).values
+    assert torch.all(srt[:, 1:] != srt[:, :-1])
+
+
 def test_all_knn_3d_10m_k10_sampled(api):
-    """3D all-kNN at full size (n = 10,000,000, k = 10) in the benchmark's
-    launch configuration; sampled rows against the oracle, properties on all."""
+    """3D all-kNN at full size (n = 10,000,000, k = 10) for the leaf sizes the
+    workload names ({8, 16, 32}, automatic traversal); sampled rows against
+    the oracle, properties on all."""
     n = 10_000_000
     pts = synth.uniform(n, 3, synth.BASE_SEED + 2)
     x = _cuda(pts)
@@ -257,12 +271,78 @@ def test_all_knn_3d_10m_k10_sampled(api):
         rows = _sample_rows(n, 400, leaf)
         o_idx, o_dist = oracle.knn(pts, pts[rows], 10, nthreads=0)
         compare_knn(idx[rows].cpu().numpy(), dist[rows].cpu().numpy(), o_idx, o_dist, pts, pts[rows])
-        d = dist
-        assert torch.all(d[:, 1:] >= d[:, :-1])
-        assert torch.all(d[:, 0] == 0)
-        assert torch.all((idx >= 0) & (idx < n))
+        _check_all_knn_rows(idx, dist, n)
         tree.free()
         del idx, dist
+
+
+@pytest.mark.parametrize("leaf,var", [(48, 3), (64, 3), (32, 1), (48, 2)],
+                         ids=["leaf48-postponed", "leaf64-postponed", "leaf32-thread", "leaf48-packet"])
+def test_all_knn_3d_10m_k10_bench_config(api, leaf, var):
+    """The benchmark's own workload and launch configuration: 10,000,000
+    uniform 3D points (the benchmark's seed), all-kNN with k = 10, the leaf
+    size and traversal named per call as the benchmark runs them; 512 sampled
+    rows against the oracle, properties on every row."""
+    n = 10_000_000
+    pts = synth.uniform(n, 3, synth.BASE_SEED + 2)
+    x = _cuda(pts)
+    tree = api.pg_tree_build(x, leaf_size=leaf)
+    idx, dist = api.pg_knn(tree, None, 10, variant=var)
+    rows = _sample_rows(n, 512, 1000 + leaf + var)
+    o_idx, o_dist = oracle.knn(pts, pts[rows], 10, nthreads=0)
+    compare_knn(idx[rows].cpu().numpy(), dist[rows].cpu().numpy(), o_idx, o_dist, pts, pts[rows])
+    _check_all_knn_rows(idx, dist, n)
+    tree.free()
+
+
+def test_per_call_variants_and_tune_table(api):
+    """The traversal is chosen per call, per thread override, or by the tune
+    table; every choice gives the same bits.  The counting instance (which
+    runs only for the postponed-leaf kernel) shows which kernel ran."""
+    import threading
+
+    pts = synth.gmm(40000, 3, 47)
+    tree = api.pg_tree_build(_cuda(pts), leaf_size=24)
+    ref = api.pg_knn(tree, None, 10, variant=api.KNN_THREAD)
+    for v in api.KNN_VARIANTS:
+        got = api.pg_knn(tree, None, 10, variant=v)
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+
+    def counted(**kw):
+        api.pg_knn_touch_read()
+        api.pg_knn_touch_enable(True)
+        try:
+            out = api.pg_knn(tree, None, 10, **kw)
+        finally:
+            api.pg_knn_touch_enable(False)
+        return out, api.pg_knn_touch_read()[1]
+
+    try:
+        api.pg_knn_tune_set(3, 10, True, api.KNN_THREAD)
+        assert api.pg_knn_tune_get(3, 9, True) == api.KNN_THREAD       # same k class (9-10)
+        out, cnt = counted()
+        assert cnt == 0 and torch.equal(out[0], ref[0])
+        api.pg_knn_tune_set(3, 10, True, api.KNN_POSTPONED)
+        out, cnt = counted()
+        assert cnt > 0 and torch.equal(out[0], ref[0])
+        api.pg_knn_set_variant(api.KNN_THREAD)                        # this thread's override wins
+        assert api.pg_knn_tune_get(3, 10, True) == api.KNN_THREAD
+        out, cnt = counted()
+        assert cnt == 0
+        out, cnt = counted(variant=api.KNN_POSTPONED)                 # an explicit variant wins
+        assert cnt > 0
+        # another thread does not see this thread's override
+        seen = {}
+        th = threading.Thread(target=lambda: seen.setdefault("v", api.pg_knn_tune_get(3, 10, True)))
+        th.start()
+        th.join()
+        assert seen["v"] == api.KNN_POSTPONED
+    finally:
+        api.pg_knn_set_variant(0)
+        api.pg_knn_tune_set(3, 10, True, api.KNN_AUTO)
+    with pytest.raises(api.PgError, match="variant"):
+        api.pg_knn(tree, None, 10, variant=99)
+    tree.free()
 
 
 @pytest.mark.parametrize("d", [5, 7])
