@@ -287,6 +287,115 @@ __device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q
     }
 }
 
+// All-kNN with postponed leaves, from the bottom: the query is bucket entry
+// `pos`, so its own leaf is known and is queued first (it gives the lane a
+// close k-th distance at once); the lane then climbs the parent links and, at
+// each ancestor, searches only the other child's subtree (every point lies in
+// the own leaf or in exactly one such sibling subtree, so the answer is the
+// same exact k-NN).  Leaves found by the walk go to a queue of two: a lane
+// that already holds a leaf keeps walking while some other lane of the warp
+// still looks for one, so fewer lanes idle in the node phase.  A queued leaf
+// is tested again against the k-th distance when it is taken.
+template <int DC, int KC, bool COUNT = false>
+__device__ __forceinline__ void search_self_ww(const TreeDesc &T, int64_t pos, const float *q, bool valid,
+                                               KList<KC> &L, unsigned &nrec, unsigned &cand) {
+    constexpr int NW = node_w(DC);
+    int s_ref[KNN_STACK], s_cnt[KNN_STACK];
+    float s_d[KNN_STACK];
+    int sp = 0, cur = -1, up = -1, qn = 0;
+    int q0r = 0, q0c = 0, q1r = 0, q1c = 0;   // leaf queue: (ref, cnt, bound), entry 0 taken first
+    float q0d = 0.f, q1d = 0.f;
+    bool done = !valid;
+    auto enqueue = [&](int r, int c, float d) {
+        if (qn == 0) { q0r = r; q0c = c; q0d = d; }
+        else { q1r = r; q1c = c; q1d = d; }
+        ++qn;
+    };
+    if (valid) {
+        const int code = __ldg(T.leaf_parent + pos);
+        if (code < 0) {
+            enqueue(T.root_ref, T.root_cnt, 0.f);
+        } else {
+            const int2 rc = __ldg(reinterpret_cast<const int2 *>(
+                reinterpret_cast<const float *>(T.nodes + (size_t)(code >> 1) * NW) + 4 * DC) + (code & 1));
+            enqueue(rc.x, rc.y, 0.f);
+        }
+        up = code;
+    }
+    for (;;) {
+        // node phase: lanes with a free queue slot advance while some lane has no leaf
+        for (;;) {
+            if (!__any_sync(0xffffffffu, !done && qn == 0)) break;
+            if (!done && qn < 2) {
+                if (cur < 0) {
+                    if (sp > 0) {
+                        --sp;
+                        if (s_d[sp] <= L.kth()) {
+                            if (s_cnt[sp] > 0) enqueue(s_ref[sp], s_cnt[sp], s_d[sp]);
+                            else cur = s_ref[sp];
+                        }
+                    } else if (up >= 0) {
+                        // climb: the other child of the next ancestor
+                        const int pn = up >> 1, other = 1 - (up & 1);
+                        const float *rec = reinterpret_cast<const float *>(T.nodes + (size_t)pn * NW);
+                        float lo[DC], hi[DC];
+#pragma unroll
+                        for (int c = 0; c < DC; ++c) {
+                            lo[c] = __ldg(rec + other * 2 * DC + c);
+                            hi[c] = __ldg(rec + other * 2 * DC + DC + c);
+                        }
+                        const int2 rc = __ldg(reinterpret_cast<const int2 *>(rec + 4 * DC) + other);
+                        up = __ldg(T.parent + pn);
+                        const float ds = boxdist<DC>(q, lo, hi);
+                        if (rc.y >= 0 && ds <= L.kth()) {
+                            if (rc.y > 0) enqueue(rc.x, rc.y, ds);
+                            else cur = rc.x;
+                        }
+                    } else {
+                        done = true;
+                    }
+                }
+                if (cur >= 0) {
+                    if (COUNT) ++nrec;
+                    float rec[4 * NW];
+                    const float4 *np = T.nodes + (size_t)cur * NW;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        float4 f = __ldg(np + w);
+                        rec[4 * w] = f.x; rec[4 * w + 1] = f.y; rec[4 * w + 2] = f.z; rec[4 * w + 3] = f.w;
+                    }
+                    const int *ri = reinterpret_cast<const int *>(rec + 4 * DC);
+                    const int r0 = ri[0], c0 = ri[1], r1 = ri[2], c1 = ri[3];
+                    const float d0 = boxdist<DC>(q, rec, rec + DC);
+                    const float d1 = boxdist<DC>(q, rec + 2 * DC, rec + 3 * DC);
+                    const bool sw = d1 < d0;
+                    const float dn = sw ? d1 : d0, df = sw ? d0 : d1;
+                    const int rn = sw ? r1 : r0, cn = sw ? c1 : c0;
+                    const int rf = sw ? r0 : r1, cf = sw ? c0 : c1;
+                    const float kth = L.kth();
+                    if (cf >= 0 && df <= kth && sp < KNN_STACK) {
+                        s_ref[sp] = rf; s_cnt[sp] = cf; s_d[sp] = df; ++sp;
+                    }
+                    cur = -1;
+                    if (cn >= 0 && dn <= kth) {
+                        if (cn > 0) enqueue(rn, cn, dn);
+                        else cur = rn;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, qn > 0)) break;
+        // leaf phase, converged: every lane takes its first queued leaf
+        int lref = 0, lcnt = 0;
+        if (qn > 0) {
+            if (q0d <= L.kth()) { lref = q0r; lcnt = q0c; }
+            q0r = q1r; q0c = q1c; q0d = q1d;
+            --qn;
+        }
+        scan_own_leaf_converged<DC, KC, true, COUNT>(T.bucket, lref, lcnt, q, L, cand);
+    }
+}
+
 template <int DC, int KC, bool COUNT = false>
 __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restrict__ trees, int ntrees,
                                                         const float *__restrict__ queries,
@@ -314,7 +423,10 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
     KList<KC> L;
     L.init(k);
     unsigned nrec = 0, cand = 0;
-    for (int t = 0; t < ntrees; ++t) search_tree_ww<DC, KC, true, COUNT>(trees[t], q, valid, L, nrec, cand);
+    if (self_bucket && trees[0].leaf_parent && trees[0].parent)
+        search_self_ww<DC, KC, COUNT>(trees[0], pos, q, valid, L, nrec, cand);
+    else
+        for (int t = 0; t < ntrees; ++t) search_tree_ww<DC, KC, true, COUNT>(trees[t], q, valid, L, nrec, cand);
     if (COUNT) {
         unsigned long long a = nrec, b = cand;
 #pragma unroll
