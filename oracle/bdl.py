@@ -18,7 +18,7 @@ Erase_L (Appendix A.3, Algorithm 4):
   * gather the points of every tree left with fewer than half of its capacity;
   * reinsert them with Insert_L.
 
-Readings where the paper is silent (each is listed in the design notes):
+Readings where the paper is silent (this model takes each of them as stated):
   * which batch points go to the buffer: the last |P| mod X of the batch, in
     batch order (a new batch is in input order; a reinserted set is in
     ascending id order);

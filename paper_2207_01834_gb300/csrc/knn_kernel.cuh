@@ -102,6 +102,21 @@ __device__ __forceinline__ void load_point(const float4 *__restrict__ bucket, in
     pid = __float_as_uint(v[DC]);
 }
 
+// True when every point within squared distance kth of q lies in the box
+// [lo, hi] (the first `dim` coordinates; padding coordinates are zero for
+// every point): q is inside and the squared gap to every face exceeds kth.
+// A point outside the box lies beyond some face, and the rounded chain of
+// sqdist is monotone in each term, so its distance is at least that face's
+// squared gap: such a point cannot be within kth.
+template <int DC>
+__device__ __forceinline__ bool ball_inside(const float *q, const float *lo, const float *hi, int dim, float kth) {
+    float g = fminf(__fsub_rn(q[0], lo[0]), __fsub_rn(hi[0], q[0]));
+#pragma unroll
+    for (int c = 1; c < DC; ++c)
+        if (c < dim) g = fminf(g, fminf(__fsub_rn(q[c], lo[c]), __fsub_rn(hi[c], q[c])));
+    return g > 0.f && __fmul_rn(g, g) > kth;
+}
+
 template <int DC, int KC, bool NC = true>
 __device__ __forceinline__ void scan_leaf(const float4 *__restrict__ bucket, int ref, int cnt, const float *q,
                                           KList<KC> &L) {
@@ -297,7 +312,7 @@ __device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q
 // still looks for one, so fewer lanes idle in the node phase.  A queued leaf
 // is tested again against the k-th distance when it is taken.
 template <int DC, int KC, bool COUNT = false>
-__device__ __forceinline__ void search_self_ww(const TreeDesc &T, int64_t pos, const float *q, bool valid,
+__device__ __forceinline__ void search_self_ww(const TreeDesc &T, int64_t pos, const float *q, int dim, bool valid,
                                                KList<KC> &L, unsigned &nrec, unsigned &cand) {
     constexpr int NW = node_w(DC);
     int s_ref[KNN_STACK], s_cnt[KNN_STACK];
@@ -335,21 +350,31 @@ __device__ __forceinline__ void search_self_ww(const TreeDesc &T, int64_t pos, c
                             else cur = s_ref[sp];
                         }
                     } else if (up >= 0) {
-                        // climb: the other child of the next ancestor
-                        const int pn = up >> 1, other = 1 - (up & 1);
+                        // climb: the other child of the next ancestor, unless
+                        // the k-th ball lies inside the subtree searched so far
+                        const int pn = up >> 1, side = up & 1, other = 1 - side;
                         const float *rec = reinterpret_cast<const float *>(T.nodes + (size_t)pn * NW);
                         float lo[DC], hi[DC];
 #pragma unroll
                         for (int c = 0; c < DC; ++c) {
-                            lo[c] = __ldg(rec + other * 2 * DC + c);
-                            hi[c] = __ldg(rec + other * 2 * DC + DC + c);
+                            lo[c] = __ldg(rec + side * 2 * DC + c);
+                            hi[c] = __ldg(rec + side * 2 * DC + DC + c);
                         }
-                        const int2 rc = __ldg(reinterpret_cast<const int2 *>(rec + 4 * DC) + other);
-                        up = __ldg(T.parent + pn);
-                        const float ds = boxdist<DC>(q, lo, hi);
-                        if (rc.y >= 0 && ds <= L.kth()) {
-                            if (rc.y > 0) enqueue(rc.x, rc.y, ds);
-                            else cur = rc.x;
+                        if (ball_inside<DC>(q, lo, hi, dim, L.kth())) {
+                            up = -1;
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < DC; ++c) {
+                                lo[c] = __ldg(rec + other * 2 * DC + c);
+                                hi[c] = __ldg(rec + other * 2 * DC + DC + c);
+                            }
+                            const int2 rc = __ldg(reinterpret_cast<const int2 *>(rec + 4 * DC) + other);
+                            up = __ldg(T.parent + pn);
+                            const float ds = boxdist<DC>(q, lo, hi);
+                            if (rc.y >= 0 && ds <= L.kth()) {
+                                if (rc.y > 0) enqueue(rc.x, rc.y, ds);
+                                else cur = rc.x;
+                            }
                         }
                     } else {
                         done = true;
@@ -424,7 +449,7 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
     L.init(k);
     unsigned nrec = 0, cand = 0;
     if (self_bucket && trees[0].leaf_parent && trees[0].parent)
-        search_self_ww<DC, KC, COUNT>(trees[0], pos, q, valid, L, nrec, cand);
+        search_self_ww<DC, KC, COUNT>(trees[0], pos, q, dim, valid, L, nrec, cand);
     else
         for (int t = 0; t < ntrees; ++t) search_tree_ww<DC, KC, true, COUNT>(trees[t], q, valid, L, nrec, cand);
     if (COUNT) {
@@ -671,7 +696,7 @@ __global__ void __launch_bounds__(PKT_THREADS) k_knn_packet(const TreeDesc *__re
 // sibling subtree, so the answer is the same exact k-NN, without the
 // top-down descent from the root.
 template <int DC, int KC>
-__device__ __forceinline__ void search_self_up(const TreeDesc &T, int64_t pos, const float *q, KList<KC> &L) {
+__device__ __forceinline__ void search_self_up(const TreeDesc &T, int64_t pos, const float *q, int dim, KList<KC> &L) {
     constexpr int NW = node_w(DC);
     int code = __ldg(T.leaf_parent + pos);
     {
@@ -687,9 +712,13 @@ __device__ __forceinline__ void search_self_up(const TreeDesc &T, int64_t pos, c
     int s_ref[KNN_STACK], s_cnt[KNN_STACK];
     float s_d[KNN_STACK];
     while (code >= 0) {
-        const int pn = code >> 1, other = 1 - (code & 1);
+        const int pn = code >> 1, side = code & 1, other = 1 - side;
         const float *rec = reinterpret_cast<const float *>(T.nodes + (size_t)pn * NW);
         float lo[DC], hi[DC];
+#pragma unroll
+        for (int c = 0; c < DC; ++c) { lo[c] = __ldg(rec + side * 2 * DC + c); hi[c] = __ldg(rec + side * 2 * DC + DC + c); }
+        // the k-th ball inside the subtree searched so far: nothing above can hold a neighbour
+        if (ball_inside<DC>(q, lo, hi, dim, L.kth())) break;
 #pragma unroll
         for (int c = 0; c < DC; ++c) { lo[c] = __ldg(rec + other * 2 * DC + c); hi[c] = __ldg(rec + other * 2 * DC + DC + c); }
         const int2 rc = __ldg(reinterpret_cast<const int2 *>(rec + 4 * DC) + other);
@@ -770,7 +799,7 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
     KList<KC> L;
     L.init(k);
     if (self_bucket && trees[0].leaf_parent && trees[0].parent) {
-        search_self_up<DC, KC>(trees[0], qi, q, L);
+        search_self_up<DC, KC>(trees[0], qi, q, dim, L);
     } else {
         for (int t = 0; t < ntrees; ++t) search_tree<DC, KC>(trees[t], q, L);
     }

@@ -167,3 +167,31 @@ def test_batch_dynamic_schedule_3d(api):
         o_idx, o_dist = oracle.knn(allp[lid], q[rows], 10, ids=lid, nthreads=0)
         compare_knn(idx[rows].cpu().numpy(), dist[rows].cpu().numpy(), o_idx, o_dist, allp[lid], q[rows], ids=lid)
         assert live[idx.cpu().numpy().ravel()].all()       # erased points are never returned
+
+
+@pytest.mark.parametrize("m", [300, 20000])
+def test_forest_variants_agree_bitwise(api, m):
+    """kNN_L over a forest with erased points: every traversal variant returns
+    the same bits (each is the exact k smallest pairs over the live set), and
+    the answer matches brute force over the live set.  20,000 queries are
+    processed in leaf order, 300 in input order."""
+    X = 512
+    f = api.BDL(3, X, leaf_size=16)
+    model = BDLModel(3, X)
+    for step in range(6):
+        p = synth.gmm(3000 + 1500 * step, 3, 600 + step)
+        f.insert(_cuda(p))
+        model.insert(p)
+        if step % 2:
+            live, _ = model.live_arrays()
+            er = live[np.random.default_rng(step).choice(len(live), size=len(live) // 5, replace=False)]
+            f.erase(_cuda(er))
+            model.erase(er)
+    assert bin(f.structure()["F"]).count("1") >= 3
+    q = synth.gmm(m, 3, 700)
+    outs = [f.knn(_cuda(q), 10, variant=v) for v in api.KNN_VARIANTS]
+    for got in outs[1:]:
+        assert torch.equal(got[0], outs[0][0]) and torch.equal(got[1], outs[0][1])
+    pts, ids = model.live_arrays()
+    o_idx, o_dist = oracle.knn(pts, q, 10, ids=ids, nthreads=0)
+    compare_knn(outs[-1][0].cpu().numpy(), outs[-1][1].cpu().numpy(), o_idx, o_dist, pts, q, ids=ids)

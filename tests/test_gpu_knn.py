@@ -186,13 +186,13 @@ def test_knn_padding(api, variant):
 
 
 def test_variants_agree_bitwise(api):
-    """Both traversal variants return the exact k smallest (float32 distance,
+    """Every traversal variant returns the exact k smallest (float32 distance,
     id) pairs, so their outputs are identical."""
     pts = synth.gmm(60000, 3, 41)
     q = synth.gmm(20000, 3, 42)
     tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
     outs = []
-    for v in (1, 2, 3):
+    for v in api.KNN_VARIANTS:
         api.pg_knn_set_variant(v)
         outs.append(api.pg_knn(tree, _cuda(q), 12) + api.pg_knn(tree, None, 7))
     api.pg_knn_set_variant(0)
