@@ -128,7 +128,7 @@ PG_API pg_status pg_tree_build_split(const float *points, int64_t n, int dim, in
  * out_idx (device, m*k int32) and out_dist (device, m*k float32).
  * k in [1, PG_MAX_K].  The traversal is PG_KNN_AUTO's choice.
  * Stream-ordered, no synchronisation.  Separate queries (m >= 4096) are first
- * ordered by the leaf they fall in (scratch of 4 * m bytes), so that a warp's
+ * ordered by the leaf they fall in (scratch of 8 * m bytes), so that a warp's
  * queries are neighbours.  Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA.
  */
 PG_API pg_status pg_knn(const pg_tree *tree, const float *queries, int64_t m, int k, int32_t *out_idx,

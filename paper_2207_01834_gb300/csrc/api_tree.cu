@@ -61,20 +61,22 @@ pg_status pg_knn_ex(const pg_tree *tree, const float *queries, int64_t m, int k,
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (tree->n == 0) {
         // Nothing to find: every slot is padding.
-        return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, nullptr, m, tree->dim, k, out_idx, out_dist,
-                          variant, s);
+        return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, nullptr, nullptr, m, tree->dim, k, out_idx,
+                          out_dist, variant, s);
     }
     if (!queries)   // all-kNN: bucket order is already tree order
-        return knn_launch(tree->desc, 1, tree->dc, nullptr, tree->bucket, nullptr, m, tree->dim, k, out_idx,
-                          out_dist, variant, s);
+        return knn_launch(tree->desc, 1, tree->dc, nullptr, tree->bucket, nullptr, nullptr, m, tree->dim, k,
+                          out_idx, out_dist, variant, s);
+    // Queries sorted by the leaf they fall in: the processing order and, per
+    // position, that leaf (where a bottom-up search starts).
     Scratch ord;
     const bool sorted = m >= kOrderMinQueries;
     if (sorted) {
-        PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)m, s));
-        PG_TRY(query_order(tree, queries, m, tree->dim, ord.as<int32_t>(), s));
+        PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)(2 * m), s));
+        PG_TRY(query_order(tree, queries, m, tree->dim, ord.as<int32_t>(), s, ord.as<int32_t>() + m));
     }
-    return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr, m, tree->dim,
-                      k, out_idx, out_dist, variant, s);
+    return knn_launch(tree->desc, 1, tree->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr,
+                      sorted ? ord.as<int32_t>() + m : nullptr, m, tree->dim, k, out_idx, out_dist, variant, s);
 }
 
 pg_status pg_tree_free(pg_tree *tree) {

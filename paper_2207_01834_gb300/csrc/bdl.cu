@@ -482,8 +482,8 @@ pg_status pg_bdl_knn_ex(const pg_bdl *b, const float *queries, int64_t m, int k,
         PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)m, b->s));
         PG_TRY(query_order(big, queries, m, b->dim, ord.as<int32_t>(), b->s));
     }
-    return knn_launch(b->forest, b->forest_n, b->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr, m, b->dim,
-                      k, out_idx, out_dist, variant, b->s);
+    return knn_launch(b->forest, b->forest_n, b->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr, nullptr,
+                      m, b->dim, k, out_idx, out_dist, variant, b->s);
 }
 
 pg_status pg_bdl_size(const pg_bdl *b, int64_t *live) {

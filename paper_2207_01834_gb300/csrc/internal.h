@@ -101,10 +101,14 @@ TreeDesc tree_desc(const pg_tree *t);
 // is the entry's id; otherwise queries are row-major m*dim floats.
 // order (may be NULL): processing order of the queries (a permutation of
 // 0..m-1 that puts queries of the same leaf next to each other).
+// start_leaf (may be NULL): per processing position, the bucket position of
+// the leaf the query falls in; traversals that search from the bottom start
+// there.  self_bucket or start_leaf may be given only with ntrees == 1 and a
+// tree that has its parent links (parent, leaf_parent).
 // variant: a PG_KNN_* traversal, or PG_KNN_AUTO for the automatic choice.
 pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
-                     const float4 *self_bucket, const int32_t *order, int64_t m, int dim, int k,
-                     int32_t *out_idx, float *out_dist, int variant, cudaStream_t s);
+                     const float4 *self_bucket, const int32_t *order, const int32_t *start_leaf, int64_t m,
+                     int dim, int k, int32_t *out_idx, float *out_dist, int variant, cudaStream_t s);
 int k_class(int k);
 bool valid_variant(int v);
 // The variant PG_KNN_AUTO resolves to for this thread and request.
@@ -114,7 +118,10 @@ constexpr int kKnnCountingInstance = 100;
 
 // ---- order.cu
 // Queries sorted by the leaf of `t` they fall in (stable); order gets m ints.
-pg_status query_order(const pg_tree *t, const float *queries, int64_t m, int dim, int32_t *order, cudaStream_t s);
+// leaf_ref (may be NULL) gets, per sorted position, the bucket position of
+// that query's leaf (m ints).
+pg_status query_order(const pg_tree *t, const float *queries, int64_t m, int dim, int32_t *order, cudaStream_t s,
+                      int32_t *leaf_ref = nullptr);
 constexpr int64_t kOrderMinQueries = 4096;
 
 }  // namespace pg

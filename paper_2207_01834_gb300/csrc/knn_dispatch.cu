@@ -15,7 +15,8 @@ namespace pg {
 
 #define PG_DECL(DCN)                                                                                      \
     pg_status knn_launch_dc##DCN(const TreeDesc *, int, const float *, const float4 *, const int32_t *,     \
-                                 int64_t, int, int, int32_t *, float *, int, unsigned long long *,         \
+                                 const int32_t *, int64_t, int, int, int32_t *, float *, int,              \
+                                 unsigned long long *,                                                     \
                                  cudaStream_t);
 PG_DECL(2) PG_DECL(3) PG_DECL(4) PG_DECL(5) PG_DECL(6) PG_DECL(7) PG_DECL(8) PG_DECL(12) PG_DECL(16)
 #undef PG_DECL
@@ -74,8 +75,8 @@ int resolve_variant(int requested, int dc, int k, bool self) {
 }
 
 pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
-                     const float4 *self_bucket, const int32_t *order, int64_t m, int dim, int k, int32_t *out_idx,
-                     float *out_dist, int requested, cudaStream_t s) {
+                     const float4 *self_bucket, const int32_t *order, const int32_t *start_leaf, int64_t m,
+                     int dim, int k, int32_t *out_idx, float *out_dist, int requested, cudaStream_t s) {
     if (m == 0) return PG_OK;
     if (!valid_variant(requested)) return fail(PG_EINVAL, "k-NN: unknown traversal variant");
     int variant = resolve_variant(requested, dc, k, self_bucket != nullptr);
@@ -88,15 +89,15 @@ pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float 
     }
     unsigned long long *touch = g_touch_dev;
     switch (dc) {
-        case 2: return knn_launch_dc2(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
-        case 3: return knn_launch_dc3(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
-        case 4: return knn_launch_dc4(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
-        case 5: return knn_launch_dc5(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
-        case 6: return knn_launch_dc6(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
-        case 7: return knn_launch_dc7(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
-        case 8: return knn_launch_dc8(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
-        case 12: return knn_launch_dc12(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
-        case 16: return knn_launch_dc16(trees_dev, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 2: return knn_launch_dc2(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 3: return knn_launch_dc3(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 4: return knn_launch_dc4(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 5: return knn_launch_dc5(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 6: return knn_launch_dc6(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 7: return knn_launch_dc7(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 8: return knn_launch_dc8(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 12: return knn_launch_dc12(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
+        case 16: return knn_launch_dc16(trees_dev, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist, variant, touch, s);
         default: return fail(PG_EUNSUPPORTED, "dimension class");
     }
 }

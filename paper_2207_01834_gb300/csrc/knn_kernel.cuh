@@ -421,12 +421,25 @@ __device__ __forceinline__ void search_self_ww(const TreeDesc &T, int64_t pos, c
     }
 }
 
-template <int DC, int KC, bool COUNT = false>
+// Where the postponed-leaf search of each query starts.  Each launch uses an
+// instance compiled for its own case only (the counting instance decides at
+// run time), since paths that are never taken still cost registers and
+// scheduling in the ones that are.
+enum WwMode : int {
+    WW_ANY = 0,     // decided per launch: the cases below, by their conditions
+    WW_TOP = 1,     // every tree from its root (forests; queries without a start leaf)
+    WW_SELF = 2,    // all-kNN: the query is bucket entry pos of the single tree
+    WW_START = 3,   // separate queries of a single tree from start_leaf[pos]
+};
+
+template <int DC, int KC, bool COUNT = false, int MODE = WW_ANY>
 __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restrict__ trees, int ntrees,
                                                         const float *__restrict__ queries,
                                                         const float4 *__restrict__ self_bucket,
-                                                        const int32_t *__restrict__ order, int64_t m, int dim, int k,
-                                                        int32_t *__restrict__ out_idx, float *__restrict__ out_dist,
+                                                        const int32_t *__restrict__ order,
+                                                        const int32_t *__restrict__ start_leaf, int64_t m, int dim,
+                                                        int k, int32_t *__restrict__ out_idx,
+                                                        float *__restrict__ out_dist,
                                                         unsigned long long *__restrict__ touch = nullptr) {
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = pos < m;
@@ -434,8 +447,9 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
     int64_t row = 0;
 #pragma unroll
     for (int c = 0; c < DC; ++c) q[c] = 0.f;
+    const bool self = MODE == WW_SELF || (MODE != WW_START && self_bucket != nullptr);
     if (valid) {
-        if (self_bucket) {
+        if (self) {
             unsigned qid;
             load_point<DC>(self_bucket, pos, q, qid);
             row = (int64_t)qid;
@@ -448,8 +462,12 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
     KList<KC> L;
     L.init(k);
     unsigned nrec = 0, cand = 0;
-    if (self_bucket && trees[0].leaf_parent && trees[0].parent)
-        search_self_ww<DC, KC, COUNT>(trees[0], pos, q, dim, valid, L, nrec, cand);
+    bool bottom = MODE == WW_SELF || MODE == WW_START;
+    if (MODE == WW_ANY)
+        bottom = (self_bucket || start_leaf) && ntrees == 1 && trees[0].leaf_parent && trees[0].parent;
+    if (bottom)
+        search_self_ww<DC, KC, COUNT>(trees[0], self ? pos : (valid ? (int64_t)start_leaf[pos] : 0), q, dim, valid,
+                                      L, nrec, cand);
     else
         for (int t = 0; t < ntrees; ++t) search_tree_ww<DC, KC, true, COUNT>(trees[t], q, valid, L, nrec, cand);
     if (COUNT) {
@@ -826,12 +844,19 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
             k_knn<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(trees, ntrees, queries,      \
                                                                                self_bucket, m, dim, k,     \
                                                                                out_idx, out_dist);         \
+        else if (variant == PG_KNN_POSTPONED && self_bucket)                                               \
+            k_knn_ww<DCN, KCN, false, WW_SELF><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(         \
+                trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);     \
+        else if (variant == PG_KNN_POSTPONED && start_leaf)                                                \
+            k_knn_ww<DCN, KCN, false, WW_START><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(        \
+                trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);     \
         else if (variant == PG_KNN_POSTPONED)                                                              \
-            k_knn_ww<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(                         \
-                trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist);                 \
+            k_knn_ww<DCN, KCN, false, WW_TOP><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(          \
+                trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);     \
         else if (variant == kKnnCountingInstance)                                                          \
             k_knn_ww<DCN, KCN, true><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(                   \
-                trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist, touch);          \
+                trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist,      \
+                touch);                                                                                    \
         else                                                                                               \
             k_knn_packet<DCN, KCN><<<ceil_div_i(m, PKT_THREADS), PKT_THREADS, 0, s>>>(                     \
                 trees, ntrees, queries, self_bucket, order, m, dim, k, out_idx, out_dist);                 \
@@ -840,7 +865,8 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
 #define PG_DEFINE_KNN_LAUNCH(DCN)                                                                          \
     namespace pg {                                                                                         \
     pg_status knn_launch_dc##DCN(const TreeDesc *trees, int ntrees, const float *queries,                  \
-                                 const float4 *self_bucket, const int32_t *order, int64_t m, int dim,      \
+                                 const float4 *self_bucket, const int32_t *order,                          \
+                                 const int32_t *start_leaf, int64_t m, int dim,                            \
                                  int k, int32_t *out_idx, float *out_dist, int variant,                    \
                                  unsigned long long *touch, cudaStream_t s) {                              \
         KTimer kt("knn_traverse", s);                                                                      \

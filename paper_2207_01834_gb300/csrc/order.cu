@@ -36,7 +36,8 @@ __global__ void k_locate(const float *__restrict__ queries, int64_t m, int dim, 
 
 }  // namespace
 
-pg_status query_order(const pg_tree *t, const float *queries, int64_t m, int dim, int32_t *order, cudaStream_t s) {
+pg_status query_order(const pg_tree *t, const float *queries, int64_t m, int dim, int32_t *order, cudaStream_t s,
+                      int32_t *leaf_ref) {
     if (m <= 0) return PG_OK;
     Scratch sk, st;
     PG_TRY(sk.alloc(sizeof(uint32_t) * (size_t)m, s));
@@ -62,6 +63,8 @@ pg_status query_order(const pg_tree *t, const float *queries, int64_t m, int dim
     uint32_t *sk_out, *sv_out;
     PG_TRY(radix_sort_pairs(keys, vals, true, tk, tv, m, bits, s, &sk_out, &sv_out));
     if (sv_out != vals) PG_CUDA(cudaMemcpyAsync(vals, sv_out, sizeof(uint32_t) * (size_t)m, cudaMemcpyDeviceToDevice, s));
+    if (leaf_ref)
+        PG_CUDA(cudaMemcpyAsync(leaf_ref, sk_out, sizeof(uint32_t) * (size_t)m, cudaMemcpyDeviceToDevice, s));
     return check_launch("query order");
 }
 
