@@ -15,6 +15,7 @@ is bracketed by barriers and the max over ranks is reported.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -151,6 +152,64 @@ def traffic_record(kernel: str, sha: str, variant: int, leaf: int):
         return None
     return d
 
+
+# ALU roofline of the traversal.  The peak is the issue limit: each SM's four
+# schedulers issue one 32-lane warp instruction per clock.  The achieved
+# figure counts only the operations the search needs (the model below) over
+# the node records and bucket entries the kernel actually loaded.
+ALU_OPS_MODEL = ("per bucket entry loaded: d subtractions, 1 multiply and d-1 fused multiply-adds of the squared "
+                 "distance, 3 for the (distance, id) key and its compare (2d+3); per node record expanded: two box "
+                 "distances, each d x (2 subtractions, 2 max, 1 multiply-add), and 4 for the near/far choice "
+                 "(10d+4)")
+
+
+def alu_ops(node_records: int, bucket_entries: int, d: int) -> float:
+    return float(bucket_entries) * (2 * d + 3) + float(node_records) * (10 * d + 4)
+
+
+def alu_peak_tops(dev, mhz: float = 2070.0):
+    """Lane operations per second at full issue (T/s), from the device's SM
+    count and the GB300's maximum SM clock."""
+    try:
+        import torch
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    except Exception:
+        sms = 152   # the GB300's SM count, where no device can be queried
+    return sms * 4 * 32 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz"
+
+
+def touch_counts(api, run):
+    """(node records, bucket entries) loaded by the postponed-leaf traversal
+    launches of `run`, from the library's counting instance."""
+    api.pg_knn_touch_read()
+    api.pg_knn_touch_enable(True)
+    try:
+        run()
+    finally:
+        api.pg_knn_touch_enable(False)
+    return api.pg_knn_touch_read()
+
+
+def alu_roofline(api, dev, run, ms: float, d: int) -> dict:
+    """The ALU roofline of one k-NN call `run` taking `ms` milliseconds."""
+    nrec, nent = touch_counts(api, run)
+    ops = alu_ops(nrec, nent, d)
+    peak, kind = alu_peak_tops(dev)
+    ach = ops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "peak_kind": kind, "unit": "T lane-ops/s",
+            "frac": ach / peak, "alg_ops": ops, "node_records": nrec, "bucket_entries": nent}
+
+
+def hbm_roofline(alg_bytes: float, ms: float, model: str) -> dict:
+    peak, kind = peaks()
+    ach = alg_bytes / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": ach / peak,
+            "alg_bytes": alg_bytes, "bytes_model": model}
+
+
+BUILD_BYTES_PER_POINT = 32
+BUILD_BYTES_MODEL = ("32 B per point: read its 12 B of coordinates, write its 16 B bucket entry, about 4 B of "
+                     "node records")
 
 PARITY_POOL = 16384   # rows of the timed output kept for the oracle comparison
 
@@ -323,7 +382,48 @@ def graph_range(api, torch, dev, timed, out):
     del xg, hg
 
 
-EXTRAS = ("2d", "graph_range", "object", "gmm", "bdl")
+def k_sweep(api, torch, dev, timed, out):
+    """k-NN throughput for k = 2..11 over BDL forests grown by batch inserts
+    of 5% of the data each: 10,000,000 points, 2D clustered and 7D uniform,
+    1,000,000 queries drawn from the data points, leaf 16, buffer 65,536.
+    Every k's answer must equal the first k columns of the k = 11 answer (the
+    same exact k smallest pairs); the oracle comparison is in the tests."""
+    from paper_2207_01834_gb300 import synth
+
+    stream = torch.cuda.current_stream()
+    for d in (2, 7):
+        pts = synth.ksweep_points(d)
+        n = len(pts)
+        x = torch.from_numpy(pts).to(dev)
+        f = api.BDL(d, 65536, 16)
+        step = n // synth.KSWEEP_BATCHES
+        ins_ms = 0.0
+        for i in range(synth.KSWEEP_BATCHES):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f.insert(x[i * step:(i + 1) * step] if i < synth.KSWEEP_BATCHES - 1 else x[i * step:])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ins_ms += e0.elapsed_time(e1)
+        q = x[torch.from_numpy(synth.ksweep_queries(n, d).astype(np.int64)).to(dev)]
+        kmax = max(synth.KSWEEP_KS)
+        top_i, top_d = f.knn(q, kmax)
+        ms, consistent = [], True
+        for k in synth.KSWEEP_KS:
+            ms.append(timed(lambda: f.knn(q, k)))
+            gi, gd = f.knn(q, k)
+            consistent = consistent and bool(torch.equal(gi, top_i[:, :k]) and torch.equal(gd, top_d[:, :k]))
+        st = f.structure()
+        name = "2d_gmm_10m" if d == 2 else f"{d}d_uniform_10m"
+        out[f"k_sweep_{name}_5pct_inserts"] = {
+            "k": list(synth.KSWEEP_KS), "knn_ms": ms, "mqps": [len(q) / (t / 1e3) / 1e6 for t in ms],
+            "queries": len(q), "insert_ms_total": ins_ms, "trees": bin(st["F"]).count("1"),
+            "buffer_live": int(st["buffer_live"]), "prefix_consistent_with_k11": consistent}
+        f.free()
+        del x, q, top_i, top_d
+
+
+EXTRAS = ("2d", "graph_range", "object", "gmm", "bdl", "ksweep")
 
 
 def other_configs(api, torch, dev, only=None):
@@ -347,7 +447,7 @@ def other_configs(api, torch, dev, only=None):
 
     out = {}
     sections = {"2d": small_2d, "graph_range": graph_range, "object": object_median, "gmm": gmm_5d_7d,
-                "bdl": bdl_schedule}
+                "bdl": bdl_schedule, "ksweep": k_sweep}
     for name in EXTRAS:
         if only is None or name in only:
             sections[name](api, torch, dev, timed, out)
@@ -362,6 +462,8 @@ def small_2d(api, torch, dev, timed, out):
     holder = {}
 
     def b2():
+        if "t" in holder:
+            holder["t"].free()
         holder["t"] = api.pg_tree_build(x, 16)
 
     def q2():
@@ -369,7 +471,10 @@ def small_2d(api, torch, dev, timed, out):
 
     bms = timed(b2)
     qms = timed(q2)
-    out["2d_20k_k5"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 20000 / qms / 1e3}
+    out["2d_20k_k5"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 20000 / qms / 1e3,
+                        "bound": "launch latency (20,000 queries fill a fraction of one wave)",
+                        "knn_roofline": alu_roofline(api, dev, q2, qms, 2)}
+    holder["t"].free()
 
 
 def object_median(api, torch, dev, timed, out):
@@ -381,6 +486,8 @@ def object_median(api, torch, dev, timed, out):
     ho = {}
 
     def bo():
+        if "t" in ho:
+            ho["t"].free()
         ho["t"] = api.pg_tree_build_split(xo, 48, api.SPLIT_OBJECT)
 
     def qo():
@@ -388,8 +495,11 @@ def object_median(api, torch, dev, timed, out):
 
     obms = timed(bo)
     oqms = timed(qo)
+    out["object_median_3d_10m_k10"] = {"build_ms": obms, "knn_ms": oqms, "knn_mqps": 1e7 / oqms / 1e3,
+                                       "build_roofline": hbm_roofline(1e7 * BUILD_BYTES_PER_POINT, obms,
+                                                                      BUILD_BYTES_MODEL),
+                                       "knn_roofline": alu_roofline(api, dev, qo, oqms, 3)}
     ho["t"].free()
-    out["object_median_3d_10m_k10"] = {"build_ms": obms, "knn_ms": oqms, "knn_mqps": 1e7 / oqms / 1e3}
 
 
 def gmm_5d_7d(api, torch, dev, timed, out):
@@ -405,6 +515,8 @@ def gmm_5d_7d(api, torch, dev, timed, out):
         h = {}
 
         def bd():
+            if "t" in h:
+                h["t"].free()
             h["t"] = api.pg_tree_build(pts, leaf_d)
 
         def qd():
@@ -412,8 +524,13 @@ def gmm_5d_7d(api, torch, dev, timed, out):
 
         bms = timed(bd)
         qms = timed(qd)
-        out[f"{d}d_gmm_2m_1mq_k16"] = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 1e6 / qms / 1e3,
-                                       "leaf_size": leaf_d, "traversal_variant": var_d}
+        rec = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 1e6 / qms / 1e3, "leaf_size": leaf_d,
+               "traversal_variant": var_d,
+               "build_roofline": hbm_roofline(2e6 * BUILD_BYTES_PER_POINT, bms, BUILD_BYTES_MODEL)}
+        if var_d == api.KNN_POSTPONED:   # the counting instance exists for this traversal
+            rec["knn_roofline"] = alu_roofline(api, dev, qd, qms, d)
+            rec["knn_roofline"]["note"] = "time includes ordering the queries by leaf"
+        out[f"{d}d_gmm_2m_1mq_k16"] = rec
         h["t"].free()
 
 
@@ -427,7 +544,22 @@ def bdl_schedule(api, torch, dev, timed, out):
     g = np.random.default_rng(77)
     chunks, live = [], np.zeros(0, bool)
     ins_ms, del_ms, q_ms = [], [], []
+    ins_bytes, del_bytes = [], []
+    q_counts = None
+
+    def rebuilt_points(before, after):
+        """Points written into trees (or the buffer) that a batch rebuilt."""
+        r = 0
+        for i in range(64):
+            if (after["F"] >> i) & 1 and (not (before["F"] >> i) & 1
+                                          or after["slot_live"][i] != before["slot_live"][i]):
+                r += int(after["slot_live"][i])
+        if after["buffer_live"] != before["buffer_live"]:
+            r += int(after["buffer_live"])
+        return r
+
     for b, (op, cnt) in enumerate(synth.bdl_schedule()):
+        before = f.structure()
         e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         qq = torch.from_numpy(synth.uniform(1_000_000, 3, synth.BASE_SEED + 500 + b)).to(dev)
         if op == "I":
@@ -451,11 +583,36 @@ def bdl_schedule(api, torch, dev, timed, out):
         torch.cuda.synchronize()
         (ins_ms if op == "I" else del_ms).append(e0.elapsed_time(e1))
         q_ms.append(e2.elapsed_time(e3))
+        moved = rebuilt_points(before, f.structure()) * BUILD_BYTES_PER_POINT
+        if op == "I":
+            ins_bytes.append(cnt * 12 + moved)
+        else:
+            del_bytes.append(cnt * 12 + moved)
+        if b == len(synth.bdl_schedule()) - 1:   # the final forest: counts of one query batch
+            q_counts = touch_counts(api, lambda: f.knn(qq, 10))
     out["bdl_3d_4m_schedule"] = {"initial_insert_4m_ms": ins_ms[0], "insert_1m_ms_mean": float(np.mean(ins_ms[1:])),
                                  "erase_500k_ms_mean": float(np.mean(del_ms)),
                                  "forest_knn_1mq_k10_ms_mean": float(np.mean(q_ms)),
                                  "forest_knn_mqps_mean": 1e6 / float(np.mean(q_ms)) / 1e3,
-                                 "live_points_end": int(f.size())}
+                                 "live_points_end": int(f.size()),
+                                 "insert_roofline": hbm_roofline(float(np.sum(ins_bytes[1:])), float(np.sum(ins_ms[1:])),
+                                                                 "12 B per batch point read + "
+                                                                 f"{BUILD_BYTES_PER_POINT} B per point of every "
+                                                                 "tree the batch rebuilt"),
+                                 "erase_roofline": hbm_roofline(float(np.sum(del_bytes)), float(np.sum(del_ms)),
+                                                                "12 B per erased point read + "
+                                                                f"{BUILD_BYTES_PER_POINT} B per point of every "
+                                                                "tree the batch rebuilt"),
+                                 "insert_rebuilt_bytes_mean": float(np.mean(ins_bytes[1:]))}
+    if q_counts is not None:
+        nrec, nent = q_counts
+        ops = alu_ops(nrec, nent, 3)
+        peak, kind = alu_peak_tops(dev)
+        ach = ops / (q_ms[-1] / 1e3) / 1e12
+        out["bdl_3d_4m_schedule"]["forest_knn_roofline"] = {
+            "bound": "alu", "achieved": ach, "peak": peak, "peak_kind": kind, "unit": "T lane-ops/s",
+            "frac": ach / peak, "alg_ops": ops, "node_records": nrec, "bucket_entries": nent,
+            "note": "the last batch's query over the final forest (time includes ordering the queries)"}
     f.free()
 
 
@@ -556,6 +713,7 @@ def run_ours(args):
     barrier()
     launches0 = api.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gc.disable()   # no collector pause inside a timed region (the host paces the launches)
     with ClockSampler(local) as clk:
         barrier()
         ev0.record(stream)
@@ -563,6 +721,7 @@ def run_ours(args):
             step()
         ev1.record(stream)
         barrier()
+    gc.enable()
     launches = api.launch_count() - launches0
     total_ms, qps = combine_ranks(dist, dev, ev0.elapsed_time(ev1), n * args.steps, ws)
     ms_per_step = total_ms / args.steps
@@ -665,13 +824,15 @@ def run_ours(args):
                 if ev is not None:
                     stream.wait_event(ev)   # the last results are on the host
 
-        e2e_run(2)
+        e2e_run(max(8, args.warmup))   # the first pipelined steps can stall once (tens of ms)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gc.disable()
         e0.record(stream)
         e2e_run(args.steps, e0)
         e1.record(stream)
         barrier()
+        gc.enable()
         e_ms, e_qps = combine_ranks(dist, dev, e0.elapsed_time(e1), n * args.steps, ws)
         e2e = {"value": e_qps / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(h_in.numel() * 4),
@@ -688,27 +849,30 @@ def run_ours(args):
     sha = kernel_sha(KNN_SOURCES)
     rec = traffic_record("knn_traverse", sha, variant, leaf)
     traffic = None if rec is None else float(rec["dram_bytes_per_unit"]) * n
-    # touched-bytes model: node records and bucket entries the traversal loads
-    # (through L1/L2), counted by the counting instance of the same kernel in
-    # one extra launch outside the timed region
+    # node records and bucket entries the traversal loads, counted by the
+    # counting instance of the same kernel in one extra launch outside the
+    # timed region: the touched-bytes model and the ALU operation model
+    nrec = nent = None
     touched = None
     if variant == 3:
         t = api.pg_tree_build(x, leaf_size=leaf)
-        api.pg_knn_touch_read()
-        api.pg_knn_touch_enable(True)
-        api.pg_knn(t, None, K, out_idx=idx, out_dist=dst, variant=variant)
-        api.pg_knn_touch_enable(False)
-        nrec, nent = api.pg_knn_touch_read()
+        nrec, nent = touch_counts(api, lambda: api.pg_knn(t, None, K, out_idx=idx, out_dist=dst, variant=variant))
         t.free()
         touched = nrec * 16 * (DIM + 1) + nent * 16 * ((DIM + 1 + 3) // 4)
-    roofline = {"bound": "hbm", "kernel": f"{KNN_KERNELS.get(variant, 'k_knn')}<3,10> (knn_traverse)",
-                "achieved": achieved, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "traffic_frac": None if traffic is None else traffic / (knn_avg_ms / 1e3) / 1e9 / peak,
-                "touched_bytes_per_launch": touched,
-                "touched_frac": None if touched is None else touched / (knn_avg_ms / 1e3) / 1e9 / peak,
-                "alg_bytes_per_launch": alg_bytes,
+    hbm = {"achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+           "alg_bytes_per_launch": alg_bytes,
+           "traffic_frac": None if traffic is None else traffic / (knn_avg_ms / 1e3) / 1e9 / peak,
+           "touched_bytes_per_launch": touched,
+           "touched_frac": None if touched is None else touched / (knn_avg_ms / 1e3) / 1e9 / peak}
+    alu_peak, alu_peak_kind = alu_peak_tops(dev)
+    ops = None if nrec is None else alu_ops(nrec, nent, DIM)
+    alu_achieved = None if ops is None else ops / (knn_avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"{KNN_KERNELS.get(variant, 'k_knn')}<3,10> (knn_traverse)",
+                "achieved": alu_achieved, "peak": alu_peak, "peak_kind": alu_peak_kind, "unit": "T lane-ops/s",
+                "frac": None if alu_achieved is None else alu_achieved / alu_peak,
+                "traffic": traffic, "alg_ops_per_launch": ops, "ops_model": ALU_OPS_MODEL,
+                "node_records_per_launch": nrec, "bucket_entries_per_launch": nent,
+                "hbm": hbm,
                 "avg_launch_ms": knn_avg_ms, "launches_timed": knn_launches,
                 "launch_ms_source": "library event timers around each traversal launch, in a second pass of the "
                                     "same steps right after the timed one",
@@ -717,9 +881,11 @@ def run_ours(args):
         roofline["cache_hit_pct"] = {"l2": rec["l2_sector_hit_pct"], "l2_reads": rec["l2_read_sector_hit_pct"],
                                      "l1": rec["l1_sector_hit_pct"], "source": "ncu, profiles/"}
     if rec is not None and "alu_pipe_pct" in rec:
-        # the unit that does bound the traversal: ALU pipe and issue slots
+        # measured utilisation of the units that bound the traversal
         roofline["pipe_util_pct"] = {"alu": rec["alu_pipe_pct"], "issue": rec["issue_active_pct"],
                                      "source": "ncu, profiles/"}
+        if "warp_inst_per_query" in rec:
+            roofline["pipe_util_pct"]["warp_inst_per_query"] = rec["warp_inst_per_query"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -729,6 +895,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}",
                        "l2": "working set per step ~1.2 GB > 129 MB L2 (no explicit flush)"},
             "build_ms": build_ms, "knn_ms": query_ms, "knn_mqps": n / (query_ms / 1e3) / 1e6,
+            "build_roofline": hbm_roofline(n * BUILD_BYTES_PER_POINT, build_ms, BUILD_BYTES_MODEL),
             "roofline": roofline, "gpu_launches": launches, "e2e": e2e,
             "clocks": clk.summary()}
     if rank == 0 and not args.no_batched:

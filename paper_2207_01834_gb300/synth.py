@@ -112,3 +112,23 @@ def bdl_schedule(initial: int = 4_000_000, insert: int = 1_000_000, erase: int =
     for _ in range(rounds):
         ops += [("I", insert), ("I", insert), ("D", erase)]
     return ops
+
+
+# k-NN throughput against k on forests built incrementally: k = 2..11, the
+# forest grown by batch inserts of 5% of the data each.
+KSWEEP_KS = tuple(range(2, 12))
+KSWEEP_BATCHES = 20
+
+
+def ksweep_points(d: int, n: int = 10_000_000) -> np.ndarray:
+    """Data of the k-sweep: 2D clustered (a varying-density Gaussian mixture
+    stands in for the paper's 2D VisualVar set) or d-dimensional uniform."""
+    if d == 2:
+        return gmm_sample(n, gmm_mixture(2, BASE_SEED + 60), BASE_SEED + 61)
+    return uniform(n, d, BASE_SEED + 60 + d)
+
+
+def ksweep_queries(n: int, d: int, count: int = 1_000_000) -> np.ndarray:
+    """Rows of the k-sweep data used as queries (the points query the
+    structure that holds them)."""
+    return pick_rows(n, min(n, count), BASE_SEED + 62 + d)

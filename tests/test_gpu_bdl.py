@@ -195,3 +195,32 @@ def test_forest_variants_agree_bitwise(api, m):
     pts, ids = model.live_arrays()
     o_idx, o_dist = oracle.knn(pts, q, 10, ids=ids, nthreads=0)
     compare_knn(outs[-1][0].cpu().numpy(), outs[-1][1].cpu().numpy(), o_idx, o_dist, pts, q, ids=ids)
+
+
+@pytest.mark.parametrize("d", [2, 7])
+def test_k_sweep_forest_by_5pct_inserts(api, d):
+    """The k-sweep workload: 10,000,000 points (2D clustered, 7D uniform)
+    inserted in 20 batches of 5%, 1,000,000 of the points as queries; for
+    k = 2..11 every answer is the prefix of the k = 11 answer, and sampled
+    rows of k = 2 and k = 11 match brute force over all points."""
+    pts = synth.ksweep_points(d)
+    n = len(pts)
+    x = _cuda(pts)
+    f = api.BDL(d, 65536, 16)
+    step = n // synth.KSWEEP_BATCHES
+    for i in range(synth.KSWEEP_BATCHES):
+        f.insert(x[i * step:(i + 1) * step] if i < synth.KSWEEP_BATCHES - 1 else x[i * step:])
+    assert f.size() == n
+    qrows = synth.ksweep_queries(n, d)
+    q = x[torch.from_numpy(qrows.astype(np.int64)).cuda()]
+    top_i, top_d = f.knn(q, 11)
+    for k in synth.KSWEEP_KS:
+        gi, gd = f.knn(q, k)
+        assert torch.equal(gi, top_i[:, :k]) and torch.equal(gd, top_d[:, :k]), k
+    rows = np.sort(synth.pick_rows(len(qrows), 48, 900 + d))
+    ids = np.arange(n, dtype=np.int64)   # ids are assigned in insertion order
+    for k in (2, 11):
+        o_idx, o_dist = oracle.knn(pts, pts[qrows[rows]], k, nthreads=0)
+        compare_knn(top_i[rows, :k].cpu().numpy(), top_d[rows, :k].cpu().numpy(), o_idx, o_dist, pts,
+                    pts[qrows[rows]], ids=ids)
+    f.free()
