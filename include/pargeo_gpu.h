@@ -109,14 +109,22 @@ PG_API pg_status pg_tree_build_split(const float *points, int64_t n, int dim, in
  *   PG_KNN_POSTPONED  one thread per query with postponed leaves: lanes walk
  *                     nodes until each holds a leaf, then scan their leaves
  *                     together;
+ *   PG_KNN_WARP       one warp per query: the lanes split each leaf's points
+ *                     and expand up to 32 nodes at a time, the k-list is
+ *                     spread over the lanes (one or two keys each) and
+ *                     merged by ballot and shuffle; for higher dimensions
+ *                     and large k;
  *   PG_KNN_AUTO       the calling thread's pg_knn_set_variant choice if set,
  *                     else the tune table entry for the request's dimension
  *                     class, k class and kind (all-kNN or separate queries)
- *                     (pg_knn_tune_set), else PG_KNN_POSTPONED. */
+ *                     (pg_knn_tune_set), else PG_KNN_WARP for dimension
+ *                     classes from 7 with k >= 16 and PG_KNN_POSTPONED
+ *                     otherwise. */
 #define PG_KNN_AUTO 0
 #define PG_KNN_THREAD 1
 #define PG_KNN_PACKET 2
 #define PG_KNN_POSTPONED 3
+#define PG_KNN_WARP 4
 
 /*
  * Exact k-NN of m query points (device, m*dim float32) against the tree's

@@ -1,6 +1,7 @@
 """Autotuner for the k-NN path's launch parameters: the tree's leaf size and
-the traversal kernel (thread per query, warp packets, postponed leaves), and
-the leaf size of the batched Chamfer path.
+the traversal kernel (thread per query, warp packets, postponed leaves, warp
+per query; the last also places the k-list across the warp's lanes instead
+of one thread's registers), and the leaf size of the batched Chamfer path.
 
 It times the candidates on the caller's own data (build + query through the C
 ABI, CUDA events, after a warm-up; the traversal is named per call, so no
@@ -23,7 +24,7 @@ from . import api
 from .build import OUT_DIR
 
 CACHE = os.path.join(OUT_DIR, "autotune.json")
-LEAF_CANDIDATES = (8, 16, 32, 48, 64)
+LEAF_CANDIDATES = (8, 16, 32, 48, 64, 128)
 VARIANT_CANDIDATES = api.KNN_VARIANTS
 BATCHED_LEAF_CANDIDATES = (8, 12, 16, 24, 32)
 _lock = threading.Lock()

@@ -835,9 +835,11 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
 
 }  // namespace pg
 
+#include "knn_warp.cuh"
+
 // Host launcher for one dimension class: picks the list capacity KC >= k and
 // the traversal kernel for the resolved variant (PG_KNN_THREAD,
-// PG_KNN_POSTPONED, the counting instance, else warp packets).
+// PG_KNN_POSTPONED, PG_KNN_WARP, the counting instance, else warp packets).
 #define PG_KNN_CASE(DCN, KCN)                                                                              \
     case KCN:                                                                                              \
         if (variant == PG_KNN_THREAD)                                                                      \
@@ -853,6 +855,9 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
         else if (variant == PG_KNN_POSTPONED)                                                              \
             k_knn_ww<DCN, KCN, false, WW_TOP><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(          \
                 trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);     \
+        else if (variant == PG_KNN_WARP)                                                                   \
+            launch_knn_warp<DCN, KCN>(trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k,     \
+                                      out_idx, out_dist, s);                                               \
         else if (variant == kKnnCountingInstance)                                                          \
             k_knn_ww<DCN, KCN, true><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(                   \
                 trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist,      \

@@ -23,7 +23,7 @@ def api():
     return a
 
 
-@pytest.fixture(params=[1, 2, 3], ids=["thread", "packet", "postponed"])
+@pytest.fixture(params=[1, 2, 3, 4], ids=["thread", "packet", "postponed", "warp"])
 def variant(api, request):
     """This thread's traversal override for the test's PG_KNN_AUTO calls."""
     api.pg_knn_set_variant(request.param)
@@ -276,8 +276,9 @@ def test_all_knn_3d_10m_k10_sampled(api):
         del idx, dist
 
 
-@pytest.mark.parametrize("leaf,var", [(48, 3), (64, 3), (32, 1), (48, 2)],
-                         ids=["leaf48-postponed", "leaf64-postponed", "leaf32-thread", "leaf48-packet"])
+@pytest.mark.parametrize("leaf,var", [(48, 3), (64, 3), (32, 1), (48, 2), (48, 4)],
+                         ids=["leaf48-postponed", "leaf64-postponed", "leaf32-thread", "leaf48-packet",
+                              "leaf48-warp"])
 def test_all_knn_3d_10m_k10_bench_config(api, leaf, var):
     """The benchmark's own workload and launch configuration: 10,000,000
     uniform 3D points (the benchmark's seed), all-kNN with k = 10, the leaf
