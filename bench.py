@@ -59,6 +59,10 @@ def parse():
                         "(for profiling)")
     p.add_argument("--batched-only", type=int, default=0, metavar="K",
                    help="time only the batched Chamfer forward + backward with this k (for profiling)")
+    p.add_argument("--profile-launches", action="store_true",
+                   help="one launch of each traversal workload in a fixed order, untimed (for an ncu capture): "
+                        "3D 10M all-kNN (postponed, leaf 48); 7D clustered 1M queries k=16 (postponed, leaf 32; "
+                        "warp per query, leaf 64); 3D forest of 6M points, 1M queries k=10")
     return p.parse_args()
 
 
@@ -134,7 +138,7 @@ def kernel_sha(names):
     return h.hexdigest()[:16]
 
 
-KNN_SOURCES = ["knn_kernel.cuh", "common.cuh", "knn_dc3.cu"]
+KNN_SOURCES = ["knn_kernel.cuh", "knn_warp.cuh", "common.cuh", "knn_dc3.cu"]
 
 
 KNN_KERNELS = {1: "k_knn", 2: "k_knn_packet", 3: "k_knn_ww"}
@@ -925,8 +929,45 @@ def extras_only(names):
     print(json.dumps({"other_configs": other_configs(api, torch, dev, only=only)}), flush=True)
 
 
+def profile_launches():
+    """One launch of each traversal workload, in the order the profiles name
+    them (nothing is timed; this is the command an ncu capture wraps)."""
+    import torch
+
+    from paper_2207_01834_gb300 import api, synth
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    x = torch.from_numpy(synth.uniform(N_POINTS, DIM, synth.BASE_SEED + 2)).to(dev)
+    t = api.pg_tree_build(x, 48)
+    api.pg_knn(t, None, K, variant=api.KNN_POSTPONED)
+    torch.cuda.synchronize()
+    t.free()
+    del x
+    mix = synth.gmm_mixture(7, synth.BASE_SEED + 3)
+    pts = torch.from_numpy(synth.gmm_sample(2_000_000, mix, synth.BASE_SEED + 37)).to(dev)
+    q = torch.from_numpy(synth.gmm_sample(1_000_000, mix, synth.BASE_SEED + 47)).to(dev)
+    for leaf, var in ((32, api.KNN_POSTPONED), (64, api.KNN_WARP)):
+        t = api.pg_tree_build(pts, leaf)
+        api.pg_knn(t, q, 16, variant=var)
+        torch.cuda.synchronize()
+        t.free()
+    del pts, q
+    f = api.BDL(3, 65536, 16)
+    for b, (op, cnt) in enumerate(synth.bdl_schedule()[:3]):
+        if op == "I":
+            f.insert(torch.from_numpy(synth.uniform(cnt, 3, synth.BASE_SEED + 100 + b)).to(dev))
+    f.knn(torch.from_numpy(synth.uniform(1_000_000, 3, synth.BASE_SEED + 500)).to(dev), K)
+    torch.cuda.synchronize()
+    f.free()
+    print(json.dumps({"profile_launches": "done"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_launches:
+        profile_launches()
+        return
     if args.batched_only > 0:
         batched_only(args)
         return
