@@ -509,7 +509,7 @@ pg_status level_segments(int S_max, int *ctl, const Segs &cur, const Segs &nxt, 
 // of a tile are few and consecutive), then one global atomic per child and
 // dimension; a child that finds its slot taken goes straight to global memory.
 template <int DC>
-__global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 6 : 4) k_part(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
+__global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 8 : 4) k_part(int64_t n, const float4 *__restrict__ P, float4 *__restrict__ Q,
                                                      const int *__restrict__ seg_of, int *__restrict__ seg_of_nx,
                                                      const int *__restrict__ start, const int *__restrict__ end,
                                                      const int *__restrict__ split_flag,
@@ -668,13 +668,13 @@ __global__ void k_obj_flags(int n, const uint32_t *__restrict__ sk, const uint32
 }
 
 constexpr int FIN_NT = 512;                  // threads of a finisher block
-constexpr size_t kFinSmemBudget = 110 * 1024;   // shared memory of a finisher block (two blocks per SM)
+constexpr size_t kFinSmemBudget = 72 * 1024;    // shared memory of a finisher block (three blocks per SM)
 
 // Segments small enough for one block's shared memory are finished by the
 // in-block builder; node slots are reserved by bucket position: segment
 // [st, en) uses slots [nb + st, nb + en - 1).
 template <int DC>
-__global__ void __launch_bounds__(FIN_NT, 2) k_finish(Segs fin, float4 *P, int leaf, int ns, int sc, const int *ctl,
+__global__ void __launch_bounds__(FIN_NT, 3) k_finish(Segs fin, float4 *P, int leaf, int ns, int sc, const int *ctl,
                                                       float4 *nodes, int *n_sdim, float *n_sval, int2 *n_range,
                                                       int *root_rec, int *depth_max, int *n_parent,
                                                       int *leaf_parent) {
