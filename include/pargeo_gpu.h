@@ -79,6 +79,16 @@ typedef struct pg_bdl pg_bdl;     /* one BDL-tree forest (opaque)               
  * Synchronises with `stream` a few times per build (it reads the root box,
  * the level loop's end flag once the expected depth is reached, the root
  * record and it uploads the tree descriptor), never once per level.
+ * Under stream capture (spatial-median split only) it waits on nothing: the
+ * level loop is enqueued as a device-driven loop (a conditional WHILE node
+ * of the graph being captured, its body captured from a side stream; capture
+ * in thread-local or relaxed mode), the finisher takes its work count from
+ * the device, and the descriptor is written by a kernel, so a build and the
+ * k-NN calls on the tree can be captured into one CUDA graph and replayed on
+ * new data of the same size.  The tree's host-side fields (pg_tree_info,
+ * pg_tree_export, range search, k-NN graph) are read back, with a wait on
+ * the tree's stream, by the first such call after the graph has run; a
+ * non-finite coordinate is then reported by that call, not by the build.
  * On success *out receives a handle owned by the caller (free with
  * pg_tree_free).  Errors: PG_EINVAL, PG_ENOMEM, PG_ECUDA.
  */

@@ -88,6 +88,7 @@ pg_status pg_tree_free(pg_tree *tree) {
 
 pg_status pg_tree_info(const pg_tree *t, pg_tree_info_t *info) {
     if (!t || !info) return fail(PG_EINVAL, "pg_tree_info: NULL argument");
+    PG_TRY(tree_sync_meta(const_cast<pg_tree *>(t)));
     memset(info, 0, sizeof(*info));
     info->n = t->n;
     info->dim = t->dim;
@@ -108,6 +109,7 @@ pg_status pg_tree_info(const pg_tree *t, pg_tree_info_t *info) {
 
 pg_status pg_tree_export(const pg_tree *t, float *nodes, int32_t *split_dim, float *split_val, float *bucket) {
     if (!t) return fail(PG_EINVAL, "pg_tree_export: tree is NULL");
+    PG_TRY(tree_sync_meta(const_cast<pg_tree *>(t)));
     cudaStream_t s = t->stream;
     const size_t nn = (size_t)t->num_nodes;
     if (nodes && nn) PG_CUDA(cudaMemcpyAsync(nodes, t->nodes, sizeof(float4) * node_w(t->dc) * nn, cudaMemcpyDeviceToHost, s));

@@ -91,7 +91,11 @@ __global__ void __launch_bounds__(BT) k_pack(const float *__restrict__ src, cons
 // Device-side control block of the level loop: the host enqueues levels with
 // launch sizes from upper bounds and never waits on a count; kernels read the
 // live values here and do nothing once the loop is done.
-enum { CTL_S = 0, CTL_NB, CTL_FIN, CTL_DONE, CTL_SCATTERS, CTL_LEVELS, CTL_ROOT_SPLIT, CTL_WORDS };
+// Control block of a level loop: live segments, level nodes so far, finisher
+// segments so far, done flag, levels that moved points, level count at the
+// end, whether the root split, the next level's index (for a loop driven by
+// the device), the finisher's next work item.
+enum { CTL_S = 0, CTL_NB, CTL_FIN, CTL_DONE, CTL_SCATTERS, CTL_LEVELS, CTL_ROOT_SPLIT, CTL_CUR, CTL_FIN_NEXT, CTL_WORDS };
 
 // Level partition in two passes over tiles of PT_ROWS x PT_THREADS points
 // (position base + row * PT_THREADS + thread):
@@ -199,8 +203,9 @@ __global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const floa
 __global__ void __launch_bounds__(1024) k_part_carry(unsigned *__restrict__ tsum, int ntiles, const int *__restrict__ T,
                                                      int *__restrict__ ctl, const int *__restrict__ fin_total, int level) {
     // end of the level: advance the control block (nothing after this kernel
-    // in the level reads it)
+    // in the level reads it); level < 0: the index is kept in the block
     if (threadIdx.x == 0 && !ctl[CTL_DONE]) {
+        if (level < 0) level = ctl[CTL_CUR]++;
         const int t = *T;
         ctl[CTL_NB] += t;
         ctl[CTL_FIN] += *fin_total;
@@ -672,15 +677,24 @@ constexpr size_t kFinSmemBudget = 72 * 1024;    // shared memory of a finisher b
 
 // Segments small enough for one block's shared memory are finished by the
 // in-block builder; node slots are reserved by bucket position: segment
-// [st, en) uses slots [nb + st, nb + en - 1).
+// [st, en) uses slots [nb + st, nb + en - 1).  Blocks take segments from the
+// control block's work counter until all ctl[CTL_FIN] are done; the points
+// are in P0 or P1 by the parity of the levels that moved them.
 template <int DC>
-__global__ void __launch_bounds__(FIN_NT, 3) k_finish(Segs fin, float4 *P, int leaf, int ns, int sc, const int *ctl,
-                                                      float4 *nodes, int *n_sdim, float *n_sval, int2 *n_range,
-                                                      int *root_rec, int *depth_max, int *n_parent,
+__global__ void __launch_bounds__(FIN_NT, 3) k_finish(Segs fin, float4 *P0, float4 *P1, int leaf, int ns, int sc,
+                                                      int *ctl, float4 *nodes, int *n_sdim, float *n_sval,
+                                                      int2 *n_range, int *root_rec, int *depth_max, int *n_parent,
                                                       int *leaf_parent) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int f = blockIdx.x;
-    const int nb = ctl[CTL_NB];
+    __shared__ int f_take;
+    float4 *P = (ctl[CTL_SCATTERS] & 1) ? P1 : P0;
+    const int nb = ctl[CTL_NB], total = ctl[CTL_FIN];
+    for (;;) {
+    if (threadIdx.x == 0) f_take = atomicAdd(&ctl[CTL_FIN_NEXT], 1);
+    __syncthreads();
+    const int f = f_take;
+    __syncthreads();
+    if (f >= total) break;
     const int st = fin.start[f], en = fin.end[f];
     const CtaTree r = cta_build_smem<DC, FIN_NT>(P, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC, smem, ns,
                                                  sc, leaf, nb + st, nodes, n_sdim, n_sval, n_range, fin.depth[f],
@@ -699,20 +713,78 @@ __global__ void __launch_bounds__(FIN_NT, 3) k_finish(Segs fin, float4 *P, int l
         }
         atomicMax(depth_max, r.depth);
     }
+    __syncthreads();   // the block's shared memory is reused by its next segment
+    }
 }
 
 // Every bucket entry records the code (2*node + side) of the leaf that holds
-// it: one thread per node slot fills its leaf children's ranges (unused
-// slots have cnt = -1; entries of a leaf root keep -1).
+// it: one thread per level node (the first ctl[CTL_NB] slots) fills its leaf
+// children's ranges (entries of a leaf root keep -1).
 template <int DC>
-__global__ void k_leaf_parents(const float4 *__restrict__ nodes, int num_nodes, int *__restrict__ leaf_parent) {
-    const int nd = blockIdx.x * blockDim.x + threadIdx.x;
-    if (nd >= num_nodes) return;
-    const int *ri = reinterpret_cast<const int *>(nodes + (size_t)nd * node_w(DC)) + 4 * DC;
+__global__ void k_leaf_parents(const float4 *__restrict__ nodes, const int *__restrict__ ctl,
+                               int *__restrict__ leaf_parent) {
+    const int nb = ctl[CTL_NB];
+    for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nb; nd += gridDim.x * blockDim.x) {
+        const int *ri = reinterpret_cast<const int *>(nodes + (size_t)nd * node_w(DC)) + 4 * DC;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const int ref = ri[2 * c], cnt = ri[2 * c + 1];
-        for (int i = 0; i < cnt; ++i) leaf_parent[ref + i] = 2 * nd + c;
+        for (int c = 0; c < 2; ++c) {
+            const int ref = ri[2 * c], cnt = ri[2 * c + 1];
+            for (int i = 0; i < cnt; ++i) leaf_parent[ref + i] = 2 * nd + c;
+        }
+    }
+}
+
+// The device-driven level loop (a build enqueued into a CUDA graph under
+// stream capture) runs while no level has ended the loop and the depth cap
+// is not passed.
+__global__ void k_level_cond(cudaGraphConditionalHandle h, const int *__restrict__ ctl, int cap) {
+    cudaGraphSetConditional(h, (!ctl[CTL_DONE] && ctl[CTL_CUR] <= cap) ? 1u : 0u);
+}
+
+// After a device-driven build: the final order is in P1 when an odd number
+// of levels moved points; it is copied to P0, which becomes the bucket.
+__global__ void k_copy_if_odd(const int *__restrict__ ctl, const float4 *__restrict__ P1, float4 *__restrict__ P0,
+                              size_t words) {
+    if (!(ctl[CTL_SCATTERS] & 1)) return;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x)
+        P0[i] = P1[i];
+}
+
+// After a device-driven build: the tree descriptor (root from the control
+// block and the finisher's root record, root box from the packed box) and the
+// host-side metadata words the library reads back when it next needs them:
+// root_ref, root_cnt, depth, level nodes, finisher segments, done, then the
+// root box (DC lows, DC highs) as float bits.
+template <int DC>
+__global__ void k_tree_meta(const int *__restrict__ ctl, const int *__restrict__ rec, const int *__restrict__ box,
+                            int n, const float4 *bucket, const float4 *nodes, const int *parent,
+                            const int *leaf_parent, TreeDesc *desc, int *meta) {
+    if (threadIdx.x != 0) return;
+    const bool root_split = ctl[CTL_ROOT_SPLIT] != 0;
+    const int fin_total = ctl[CTL_FIN];
+    int root_ref = 0, root_cnt = root_split ? 0 : n;
+    if (!root_split && fin_total > 0) { root_ref = rec[0]; root_cnt = rec[1]; }
+    TreeDesc d;
+    d.bucket = bucket;
+    d.nodes = nodes;
+    d.parent = parent;
+    d.leaf_parent = leaf_parent;
+    d.root_ref = root_ref;
+    d.root_cnt = root_cnt;
+    for (int c = 0; c < PG_MAX_DIM; ++c) {
+        d.root_lo[c] = c < DC ? o2f(box[c]) : 0.f;
+        d.root_hi[c] = c < DC ? o2f(box[DC + c]) : 0.f;
+    }
+    *desc = d;
+    meta[0] = root_ref;
+    meta[1] = root_cnt;
+    meta[2] = max(ctl[CTL_LEVELS], fin_total > 0 ? rec[2] : 0);
+    meta[3] = ctl[CTL_NB];
+    meta[4] = fin_total;
+    meta[5] = ctl[CTL_DONE];
+    for (int c = 0; c < DC; ++c) {
+        meta[8 + c] = __float_as_int(d.root_lo[c]);
+        meta[8 + PG_MAX_DIM + c] = __float_as_int(d.root_hi[c]);
     }
 }
 
@@ -738,7 +810,11 @@ __global__ void k_level0_init(int n, const int *__restrict__ box, Segs cur, int 
 
 template <int DC>
 struct Builder {
-    static pg_status run(float4 *packed, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t);
+    // deferred: the stream is being captured into a CUDA graph, so nothing
+    // may wait on the host; the level loop becomes a device-driven loop and
+    // the tree's host-side metadata is read back when it is next needed.
+    static pg_status run(float4 *packed, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t,
+                         bool deferred);
 };
 
 pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
@@ -780,7 +856,8 @@ pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
 }
 
 template <int DC>
-pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t) {
+pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t,
+                           bool deferred) {
     constexpr int W = bucket_w(DC);
     // Split segments hold more than `leaf` points and are disjoint, so a level
     // has at most 2*floor(n/(leaf+1)) segments.
@@ -865,6 +942,99 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
         opflag = reinterpret_cast<int *>(oks2 + n);
         ofirst = opflag + n;
     }
+    if (deferred) {
+        if (rule == PG_SPLIT_OBJECT || fin_max <= 0)
+            return fail(PG_EUNSUPPORTED, "tree build under stream capture: spatial-median split only");
+        // Every segment of a level list is a child of a segment with more
+        // than fin_max points, so a fixed slot count bounds every level.
+        const int S_fix = (int)std::min<int64_t>(seg_cap, 2 * (n / (fin_max + 1)) + 2);
+        Scratch sScan;
+        int *scan_ws = nullptr;
+        if (S_fix > kHeadMax) {
+            PG_TRY(sScan.alloc(sizeof(int) * (size_t)scan_ws_words(S_fix), s));
+            scan_ws = sScan.as<int>();
+        }
+        // Graph being captured and its current dependencies: a WHILE node goes
+        // after them, its body is captured from a side stream.
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        cudaGraph_t graph = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *edges = nullptr;
+        size_t ndeps = 0;
+        PG_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, &edges, &ndeps));
+        if (cst != cudaStreamCaptureStatusActive) return fail(PG_ECUDA, "tree build: stream capture not active");
+        cudaGraphConditionalHandle cond;
+        PG_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t loop_node;
+        PG_CUDA(cudaGraphAddNode(&loop_node, graph, deps, edges, ndeps, &cp));
+        cudaStream_t side;
+        PG_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        pg_status st = PG_OK;
+        cudaError_t e = cudaStreamBeginCaptureToGraph(side, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            // body: two levels (the ping-pong buffers swap roles), then the test
+            float4 *Pa = P, *Pb = Q;
+            int *sa = seg_of, *sb = seg_of_nx;
+            Segs ca = cur, cb = nxt;
+            const int *T = split_rank + S_fix;
+            for (int half = 0; half < 2 && st == PG_OK; ++half) {
+                st = level_segments<DC>(S_fix, ctl, ca, cb, leaf, fin_max, split_flag, split_rank, sdim, sval,
+                                        fin_flag, fin_rank, fin, t->nodes, t->split_dim, t->split_val,
+                                        t->node_range, t->parent, nullptr, 0, scan_ws, side);
+                if (st != PG_OK) break;
+                k_part_tiles<DC><<<ntiles, PT_THREADS, 0, side>>>(n, Pa, sa, split_flag, sdim, sval, T, tsum, twords);
+                k_part_carry<<<1, 1024, 0, side>>>(tsum, ntiles, T, ctl, fin_rank + S_fix, -1);
+                k_part<DC><<<ntiles, PT_THREADS, 0, side>>>(n, Pa, Pb, sa, sb, ca.start, ca.end, split_flag,
+                                                            split_rank, tsum, twords, cb.start, cb.end, cb.lo, cb.hi,
+                                                            T);
+                for (int c = 0; c < 3; ++c) count_launch();
+                std::swap(Pa, Pb);
+                std::swap(sa, sb);
+                std::swap(ca, cb);
+            }
+            k_level_cond<<<1, 1, 0, side>>>(cond, ctl, PG_DEPTH_CAP + 1);
+            count_launch();
+            e = cudaGetLastError();
+            cudaGraph_t body_out = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(side, &body_out);
+            if (e == cudaSuccess) e = e2;
+        }
+        cudaStreamDestroy(side);
+        if (st != PG_OK) return st;
+        PG_CUDA(e);
+        PG_CUDA(cudaStreamUpdateCaptureDependencies(s, &loop_node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        // after the loop: finisher, leaf codes, final order into P0, descriptor
+        Scratch sRec;
+        PG_TRY(sRec.alloc(sizeof(int) * 3, s));
+        int *rec = sRec.as<int>();
+        PG_TRY(fill_words(rec, 0u, 3, s));
+        PG_CUDA(cudaFuncSetAttribute(k_finish<DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fin_smem));
+        k_finish<DC><<<num_sms() * 3, FIN_NT, fin_smem, s>>>(fin, P0, sP1.as<float4>(), leaf, fin_max, fin_sc, ctl,
+                                                              t->nodes, t->split_dim, t->split_val, t->node_range,
+                                                              rec, rec + 2, t->parent, t->leaf_parent);
+        k_leaf_parents<DC><<<num_sms() * 8, BT, 0, s>>>(t->nodes, ctl, t->leaf_parent);
+        k_copy_if_odd<<<num_sms() * 8, BT, 0, s>>>(ctl, sP1.as<float4>(), P0, (size_t)W * n);
+        for (int c = 0; c < 3; ++c) count_launch();
+        PG_TRY(check_launch("build (device-driven) finish"));
+        if (!t->desc) PG_TRY(dalloc_n(&t->desc, 1, s));
+        if (!t->meta) PG_TRY(dalloc_n(&t->meta, (size_t)kTreeMetaWords, s));
+        k_tree_meta<DC><<<1, 32, 0, s>>>(ctl, rec, box, (int)n, P0, t->nodes, t->parent, t->leaf_parent, t->desc,
+                                         t->meta);
+        count_launch();
+        PG_TRY(check_launch("build (device-driven) descriptor"));
+        t->bucket = P0;
+        t->meta_pending = true;
+        t->num_nodes = (int)std::min<int64_t>(slots, INT32_MAX);   // until read back: every reserved slot
+        t->depth = -1;
+        t->root_ref = -1;
+        t->root_cnt = 0;
+        return PG_OK;
+    }
     int hctl[CTL_WORDS] = {0};
     int level = 0;
     for (; level <= PG_DEPTH_CAP + 1; ++level) {
@@ -935,9 +1105,9 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
         PG_TRY(fill_words(rec, 0u, 3, s));
         {
             KTimer kt("build_finish", s);
-            k_finish<DC><<<fin_total, FIN_NT, fin_smem, s>>>(fin, P, leaf, fin_max, fin_sc, ctl, t->nodes,
-                                                             t->split_dim, t->split_val, t->node_range, rec, rec + 2,
-                                                             t->parent, t->leaf_parent);
+            k_finish<DC><<<std::min(fin_total, num_sms() * 3), FIN_NT, fin_smem, s>>>(
+                fin, P0, sP1.as<float4>(), leaf, fin_max, fin_sc, ctl, t->nodes, t->split_dim, t->split_val,
+                t->node_range, rec, rec + 2, t->parent, t->leaf_parent);
             count_launch();
         }
         PG_TRY(check_launch("build finish"));
@@ -952,7 +1122,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
     // leaves of finisher segments were recorded by the finisher; the level
     // nodes' leaf children are recorded here
     if (nb > 0) {
-        k_leaf_parents<DC><<<ceil_div_i(nb, BT), BT, 0, s>>>(t->nodes, nb, t->leaf_parent);
+        k_leaf_parents<DC><<<ceil_div_i(nb, BT), BT, 0, s>>>(t->nodes, ctl, t->leaf_parent);
         count_launch();
     }
     // The final array becomes the bucket; the other ping-pong buffer is freed.
@@ -1110,7 +1280,7 @@ pg_status forest_levels(int dc, const ForestArgs &fa, cudaStream_t s) {
 
 // Packs and builds in one go (the packed array is allocated here).
 static pg_status build_from(const float *src, const int32_t *rows, const int32_t *ids, int64_t n, int dim,
-                            int leaf, int rule, cudaStream_t s, pg_tree *t) {
+                            int leaf, int rule, cudaStream_t s, pg_tree *t, bool allow_deferred) {
     const int dc = dim_class(dim);
     t->n = n;
     t->dim = dim;
@@ -1133,9 +1303,25 @@ static pg_status build_from(const float *src, const int32_t *rows, const int32_t
         dfree(packed, s);
         return PG_ENOMEM;
     }
+    // Under stream capture nothing may wait on the host: the build is
+    // enqueued device-driven and its host-side metadata read back later.
+    bool deferred = false;
+    if (allow_deferred) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) {
+            dfree(packed, s);
+            return cuda_fail(cudaGetLastError(), "cudaStreamIsCapturing");
+        }
+        deferred = cst == cudaStreamCaptureStatusActive;
+    }
     pg_status st = PG_OK;
     PG_DC_SWITCH(dc, st = pack_impl<DCV>(src, rows, ids, n, dim, packed, box.as<int>(), s));
     if (st != PG_OK) { dfree(packed, s); return st; }
+    if (deferred) {   // root box, descriptor and finite check stay on the device
+        PG_DC_SWITCH(dc, st = Builder<DCV>::run(packed, box.as<int>(), n, leaf, rule, s, t, true));
+        if (st != PG_OK && t->bucket != packed) dfree(packed, s);
+        return st;
+    }
     int hbox[2 * PG_MAX_DIM];
     PG_TRY(read_small(hbox, box.as<int>(), sizeof(int) * 2 * dc, s));
     for (int c = 0; c < PG_MAX_DIM; ++c) { t->root_lo[c] = 0.f; t->root_hi[c] = 0.f; }
@@ -1153,7 +1339,7 @@ static pg_status build_from(const float *src, const int32_t *rows, const int32_t
             return fail(PG_EINVAL, "points must have finite coordinates");
         }
     }
-    PG_DC_SWITCH(dc, st = Builder<DCV>::run(packed, box.as<int>(), n, leaf, rule, s, t));
+    PG_DC_SWITCH(dc, st = Builder<DCV>::run(packed, box.as<int>(), n, leaf, rule, s, t, false));
     if (st != PG_OK) {
         if (t->bucket != packed) dfree(packed, s);
         return st;
@@ -1162,12 +1348,33 @@ static pg_status build_from(const float *src, const int32_t *rows, const int32_t
 }
 
 pg_status build_rows(const float *pts, int64_t n, int dim, int leaf, int rule, cudaStream_t s, pg_tree *t) {
-    return build_from(pts, nullptr, nullptr, n, dim, leaf, rule, s, t);
+    return build_from(pts, nullptr, nullptr, n, dim, leaf, rule, s, t, true);
 }
 
 pg_status build_gather(const float *store, const int32_t *ids, int64_t n, int dim, int leaf, cudaStream_t s,
                        pg_tree *t) {
-    return build_from(store, ids, ids, n, dim, leaf, PG_SPLIT_SPATIAL, s, t);
+    return build_from(store, ids, ids, n, dim, leaf, PG_SPLIT_SPATIAL, s, t, false);
+}
+
+pg_status tree_sync_meta(pg_tree *t) {
+    if (!t->meta_pending) return PG_OK;
+    int h[kTreeMetaWords];
+    PG_TRY(read_small(h, t->meta, sizeof(h), t->stream));
+    if (!h[5]) return fail(PG_ECUDA, "tree build: level count exceeded the depth cap");
+    t->root_ref = h[0];
+    t->root_cnt = h[1];
+    t->depth = h[2];
+    t->num_nodes = h[4] > 0 ? h[3] + (int)t->n : h[3];
+    for (int c = 0; c < PG_MAX_DIM; ++c) {
+        const bool in = c < t->dc;
+        int a = in ? h[8 + c] : 0, b = in ? h[8 + PG_MAX_DIM + c] : 0;
+        memcpy(&t->root_lo[c], &a, 4);
+        memcpy(&t->root_hi[c], &b, 4);
+        if (in && (!std::isfinite(t->root_lo[c]) || !std::isfinite(t->root_hi[c])))
+            return fail(PG_EINVAL, "points must have finite coordinates");
+    }
+    t->meta_pending = false;
+    return PG_OK;
 }
 
 TreeDesc tree_desc(const pg_tree *t) {
@@ -1188,7 +1395,9 @@ pg_status tree_upload_desc(pg_tree *t) {
     TreeDesc d = tree_desc(t);
     static_assert(sizeof(TreeDesc) <= kStoreSmallBytes && sizeof(TreeDesc) % 4 == 0, "descriptor size");
     PG_TRY(store_small(t->desc, &d, sizeof(d), t->stream));
-    PG_CUDA(cudaStreamSynchronize(t->stream));
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    PG_CUDA(cudaStreamIsCapturing(t->stream, &cst));
+    if (cst == cudaStreamCaptureStatusNone) PG_CUDA(cudaStreamSynchronize(t->stream));
     return PG_OK;
 }
 
@@ -1202,6 +1411,9 @@ void tree_release(pg_tree *t) {
     dfree(t->parent, s);
     dfree(t->leaf_parent, s);
     dfree(t->desc, s);
+    dfree(t->meta, s);
+    t->meta = nullptr;
+    t->meta_pending = false;
     t->bucket = nullptr;
     t->nodes = nullptr;
     t->split_dim = nullptr;

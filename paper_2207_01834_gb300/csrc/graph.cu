@@ -84,6 +84,7 @@ using namespace pg;
 extern "C" pg_status pg_knn_graph(const pg_tree *tree, int k, int64_t capacity, int32_t *out_edges,
                                   int64_t *out_count, void *stream) {
     if (!tree || !out_count) return fail(PG_EINVAL, "pg_knn_graph: NULL argument");
+    PG_TRY(tree_sync_meta(const_cast<pg_tree *>(tree)));
     if (k < 1 || k >= PG_MAX_K) return fail(PG_EINVAL, "pg_knn_graph: k must be in [1, 63]");
     if (capacity < 0) return fail(PG_EINVAL, "pg_knn_graph: capacity must be >= 0");
     *out_count = 0;

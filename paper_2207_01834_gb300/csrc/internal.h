@@ -28,6 +28,11 @@ struct pg_tree {
     pg::TreeDesc *desc = nullptr;  // device copy of this tree's descriptor
     cudaStream_t stream = nullptr;
     int64_t live = 0;            // live points (BDL trees lose points on erase)
+    // A build enqueued under stream capture leaves its root, depth, node count
+    // and root box in device memory (meta); they are read back into the
+    // fields above when a host-side call first needs them.
+    int *meta = nullptr;
+    bool meta_pending = false;
 };
 
 namespace pg {
@@ -94,6 +99,11 @@ pg_status forest_levels(int dc, const ForestArgs &fa, cudaStream_t s);
 
 pg_status tree_upload_desc(pg_tree *t);
 TreeDesc tree_desc(const pg_tree *t);
+// Words of a tree's device metadata block (see k_tree_meta in build.cu).
+constexpr int kTreeMetaWords = 8 + 2 * PG_MAX_DIM;
+// Read back the host-side metadata of a tree built under stream capture
+// (waits for its stream); a no-op for other trees.
+pg_status tree_sync_meta(pg_tree *t);
 
 // ---- knn_dispatch.cu
 // k-NN over `ntrees` trees described in device memory.  If self_bucket is not

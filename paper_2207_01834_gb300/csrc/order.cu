@@ -14,14 +14,17 @@ namespace {
 
 constexpr int BT = 256;
 
+// The root comes from the tree's device descriptor, so the ordering needs no
+// host-side copy of it (a leaf or empty root gives every query key 0).
 template <int DC>
-__global__ void k_locate(const float *__restrict__ queries, int64_t m, int dim, const float4 *__restrict__ nodes,
-                         const int *__restrict__ split_dim, const float *__restrict__ split_val, int root_ref,
-                         int root_cnt, uint32_t *__restrict__ keys) {
+__global__ void k_locate(const float *__restrict__ queries, int64_t m, int dim, const TreeDesc *__restrict__ desc,
+                         const int *__restrict__ split_dim, const float *__restrict__ split_val,
+                         uint32_t *__restrict__ keys) {
     constexpr int NW = node_w(DC);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    int ref = root_ref, cnt = root_cnt;
+    const float4 *__restrict__ nodes = desc->nodes;
+    int ref = desc->root_ref, cnt = desc->root_cnt;
     for (int guard = 0; cnt == 0 && guard <= PG_DEPTH_CAP; ++guard) {
         const int sd = split_dim[ref];
         const float x = queries[i * dim + sd];
@@ -45,13 +48,10 @@ pg_status query_order(const pg_tree *t, const float *queries, int64_t m, int dim
     uint32_t *keys = sk.as<uint32_t>();
     uint32_t *tk = st.as<uint32_t>(), *tv = tk + m;
     uint32_t *vals = reinterpret_cast<uint32_t *>(order);
-    if (t->root_cnt != 0 || t->num_nodes == 0) {
-        // a leaf (or empty) root: every query shares it
-        PG_CUDA(cudaMemsetAsync(keys, 0, sizeof(uint32_t) * (size_t)m, s));
-    } else {
+    {
         const int grid = std::max(1, ceil_div_i(m, BT));
         switch (t->dc) {
-#define PG_LOC(D) case D: k_locate<D><<<grid, BT, 0, s>>>(queries, m, dim, t->nodes, t->split_dim, t->split_val, t->root_ref, t->root_cnt, keys); break;
+#define PG_LOC(D) case D: k_locate<D><<<grid, BT, 0, s>>>(queries, m, dim, t->desc, t->split_dim, t->split_val, keys); break;
             PG_LOC(2) PG_LOC(3) PG_LOC(4) PG_LOC(5) PG_LOC(6) PG_LOC(7) PG_LOC(8) PG_LOC(12) PG_LOC(16)
 #undef PG_LOC
             default: return fail(PG_EUNSUPPORTED, "dimension class");

@@ -173,6 +173,7 @@ using namespace pg;
 extern "C" pg_status pg_range(const pg_tree *tree, const float *queries, int64_t m, float radius, int64_t capacity,
                               int32_t *out_idx, int64_t *out_offsets, int64_t *out_total, void *stream) {
     if (!tree || !out_offsets || !out_total) return fail(PG_EINVAL, "pg_range: NULL argument");
+    PG_TRY(tree_sync_meta(const_cast<pg_tree *>(tree)));
     PG_TRY(range_args(tree, queries, m, radius, capacity));
     *out_total = 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -222,6 +223,7 @@ extern "C" pg_status pg_range(const pg_tree *tree, const float *queries, int64_t
 extern "C" pg_status pg_range_fill(const pg_tree *tree, const float *queries, int64_t m, float radius,
                                    const int64_t *offsets, int64_t capacity, int32_t *out_idx, void *stream) {
     if (!tree) return fail(PG_EINVAL, "pg_range_fill: NULL tree");
+    PG_TRY(tree_sync_meta(const_cast<pg_tree *>(tree)));
     PG_TRY(range_args(tree, queries, m, radius, capacity));
     if (m == 0 || tree->n == 0) return PG_OK;   // every row is empty
     if (!offsets || !out_idx) return fail(PG_EINVAL, "pg_range_fill: NULL offsets or out_idx");

@@ -1,0 +1,103 @@
+"""A build + k-NN step captured into one CUDA graph.
+
+Under stream capture pg_tree_build waits on nothing: its level loop becomes a
+device-driven loop (a WHILE node of the graph), the finisher takes its work
+count from the device, and the tree's descriptor is written by a kernel.  The
+replayed graph must give the same bits as the same calls made eagerly, for
+the captured data and for new data copied into the captured input buffer."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2207_01834_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_01834_gb300 import api as a
+    return a
+
+
+def _eager(api, x, q, k, leaf):
+    t = api.pg_tree_build(x, leaf)
+    out = api.pg_knn(t, None, k) + api.pg_knn(t, q, k)
+    info = t.info()
+    t.free()
+    return out, info
+
+
+def _data(kind, n, seed):
+    return synth.uniform(n, 3, seed) if kind == "uniform" else synth.gmm(n, 3, seed)
+
+
+@pytest.mark.parametrize("kind,n,m,leaf", [("uniform", 300_000, 20_000, 16), ("gmm", 200_000, 10_000, 48),
+                                           ("uniform", 2_000, 5_000, 8)])
+def test_captured_build_and_knn_replays_exactly(api, kind, n, m, leaf):
+    k = 10
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(_data(kind, n, 31)).to(dev)
+    q = torch.from_numpy(_data(kind, m, 32)).to(dev)
+    ref, _ = _eager(api, x, q, k, leaf)              # also warms up the library outside the capture
+    out = [torch.empty_like(a) for a in ref]
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+            t = api.pg_tree_build(x, leaf)
+            api.pg_knn(t, None, k, out_idx=out[0], out_dist=out[1])
+            api.pg_knn(t, q, k, out_idx=out[2], out_dist=out[3])
+            t.free()
+    torch.cuda.current_stream().wait_stream(side)
+    for rep in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(out, ref):
+            assert torch.equal(a, b), rep
+    # new data in the captured buffers: same bits as an eager run on it
+    x.copy_(torch.from_numpy(_data(kind, n, 33)).to(dev))
+    q.copy_(torch.from_numpy(_data(kind, m, 34)).to(dev))
+    g.replay()
+    torch.cuda.synchronize()
+    ref2, _ = _eager(api, x, q, k, leaf)
+    for a, b in zip(out, ref2):
+        assert torch.equal(a, b)
+
+
+def test_tree_built_under_capture_reads_back_its_metadata(api):
+    """A tree built inside a capture and kept afterwards: once the graph has
+    run, host-side calls (info, export-based checks) see the same tree as an
+    eager build."""
+    dev = torch.device("cuda:0")
+    pts = synth.gmm(100_000, 3, 35)
+    x = torch.from_numpy(pts).to(dev)
+    t0 = api.pg_tree_build(x, 16)
+    want = t0.info()
+    exp0 = t0.export()
+    t0.free()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    holder = {}
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+            holder["t"] = api.pg_tree_build(x, 16)
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    t = holder["t"]
+    got = t.info()
+    for f in ("n", "dim", "num_nodes", "depth", "root_ref", "root_cnt"):
+        assert getattr(got, f) == getattr(want, f), f
+    assert np.array_equal(np.array(got.root_lo), np.array(want.root_lo))
+    exp1 = t.export()
+    for key in ("bucket", "nodes"):   # (split arrays hold garbage in unused slots)
+        assert np.array_equal(np.asarray(exp1[key]).view(np.uint32), np.asarray(exp0[key]).view(np.uint32)), key
+    t.free()
+    del g   # the graph's allocations: the tree's memory was freed above
