@@ -36,8 +36,10 @@ def _data(kind, n, seed):
     return synth.uniform(n, 3, seed) if kind == "uniform" else synth.gmm(n, 3, seed)
 
 
+# 25M points: the level lists can exceed the one-block head's 16384 slots, so
+# the captured loop uses classify + device-wide scans + link
 @pytest.mark.parametrize("kind,n,m,leaf", [("uniform", 300_000, 20_000, 16), ("gmm", 200_000, 10_000, 48),
-                                           ("uniform", 2_000, 5_000, 8)])
+                                           ("uniform", 2_000, 5_000, 8), ("uniform", 25_000_000, 100_000, 48)])
 def test_captured_build_and_knn_replays_exactly(api, kind, n, m, leaf):
     k = 10
     dev = torch.device("cuda:0")
