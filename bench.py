@@ -762,11 +762,12 @@ def e2e_pipelined(api, torch, dev, pts, leaf, variant, args, stream, barrier, di
     run(max(8, args.warmup))
     barrier()
     gc.disable()
-    e0, e1 = run(args.steps)
-    barrier()
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        e0, e1 = run(args.steps)
+        barrier()
     gc.enable()
     e_ms, e_qps = combine_ranks(dist, dev, e0.elapsed_time(e1), n * args.steps, ws)
-    return {"value": e_qps / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h_in.numel() * 4),
+    return {"value": e_qps / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h_in.numel() * 4), "clocks": clk.summary(),
             "d2h_bytes_per_step": int(workers[0]["h_idx"].numel() * 4 + workers[0]["h_dst"].numel() * 4),
             "pipelined": f"{E2E_WORKERS} host threads take every other step, each with its own compute and copy "
                          "streams: one's uploads, downloads and host waits overlap the other's compute"}

@@ -690,30 +690,30 @@ __global__ void __launch_bounds__(FIN_NT, 3) k_finish(Segs fin, float4 *P0, floa
     float4 *P = (ctl[CTL_SCATTERS] & 1) ? P1 : P0;
     const int nb = ctl[CTL_NB], total = ctl[CTL_FIN];
     for (;;) {
-    if (threadIdx.x == 0) f_take = atomicAdd(&ctl[CTL_FIN_NEXT], 1);
-    __syncthreads();
-    const int f = f_take;
-    __syncthreads();
-    if (f >= total) break;
-    const int st = fin.start[f], en = fin.end[f];
-    const CtaTree r = cta_build_smem<DC, FIN_NT>(P, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC, smem, ns,
-                                                 sc, leaf, nb + st, nodes, n_sdim, n_sval, n_range, fin.depth[f],
-                                                 n_parent, leaf_parent,
-                                                 fin.parent[f] >= 0 ? 2 * fin.parent[f] + fin.side[f] : -1);
-    if (threadIdx.x == 0) {
-        const int p = fin.parent[f];
-        if (p >= 0) {
-            int *ri = reinterpret_cast<int *>(nodes + (size_t)p * node_w(DC)) + 4 * DC;
-            const int c = fin.side[f];
-            ri[2 * c] = r.root_ref;
-            ri[2 * c + 1] = r.root_cnt;
-        } else {
-            root_rec[0] = r.root_ref;
-            root_rec[1] = r.root_cnt;
+        if (threadIdx.x == 0) f_take = atomicAdd(&ctl[CTL_FIN_NEXT], 1);
+        __syncthreads();
+        const int f = f_take;
+        __syncthreads();
+        if (f >= total) break;
+        const int st = fin.start[f], en = fin.end[f];
+        const CtaTree r = cta_build_smem<DC, FIN_NT>(P, st, en, fin.lo + (size_t)f * DC, fin.hi + (size_t)f * DC, smem, ns,
+                                                     sc, leaf, nb + st, nodes, n_sdim, n_sval, n_range, fin.depth[f],
+                                                     n_parent, leaf_parent,
+                                                     fin.parent[f] >= 0 ? 2 * fin.parent[f] + fin.side[f] : -1);
+        if (threadIdx.x == 0) {
+            const int p = fin.parent[f];
+            if (p >= 0) {
+                int *ri = reinterpret_cast<int *>(nodes + (size_t)p * node_w(DC)) + 4 * DC;
+                const int c = fin.side[f];
+                ri[2 * c] = r.root_ref;
+                ri[2 * c + 1] = r.root_cnt;
+            } else {
+                root_rec[0] = r.root_ref;
+                root_rec[1] = r.root_cnt;
+            }
+            atomicMax(depth_max, r.depth);
         }
-        atomicMax(depth_max, r.depth);
-    }
-    __syncthreads();   // the block's shared memory is reused by its next segment
+        __syncthreads();   // the block's shared memory is reused by its next segment
     }
 }
 
