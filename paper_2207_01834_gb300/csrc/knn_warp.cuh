@@ -111,6 +111,17 @@ __device__ __forceinline__ void wq_insert_passing(unsigned long long kx, WarpLis
 template <int DC, int KC>
 __device__ __forceinline__ void wq_scan(const float4 *__restrict__ bucket, int ref, int cnt, const float *q,
                                         WarpList<KC> &L, int lane) {
+    if (cnt <= 32) {   // one entry per lane
+        unsigned long long k0 = WQ_NONE;
+        if (lane < cnt) {
+            float p0[DC];
+            unsigned id0;
+            load_point<DC>(bucket, ref + lane, p0, id0);
+            k0 = pair_key(sqdist<DC>(q, p0), id0);
+        }
+        wq_insert_passing<KC>(k0, L, lane);
+        return;
+    }
     for (int base = 0; base < cnt; base += 64) {
         const bool ok0 = base + lane < cnt, ok1 = base + 32 + lane < cnt;
         float p0[DC], p1[DC];
