@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "M kNN queries/s @3D 10M k=10; build s; %HBM peak; batched fwd+bwd vs plain"
+WORKLOAD = "3D all-kNN, n=10,000,000 uniform [0,1)^3, k=10, queries = all points"
+L2_NOTE = "working set per step ~1.2 GB > 129 MB L2 (no explicit flush)"
 UNIT = "M queries/s"
 N_POINTS = 10_000_000
 DIM = 3
@@ -680,8 +682,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "3D all-kNN, n=10,000,000 uniform [0,1)^3, k=10",
-                                             "n": args.n, "dim": DIM, "k": K},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": args.n, "dim": DIM, "k": K,
+                                             "parallelism": f"replicas x{ws}", "l2": L2_NOTE},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{m} queries per step against all {args.n} points"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -955,10 +957,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "3D all-kNN, n=10,000,000 uniform [0,1)^3, k=10, queries = all points",
-                       "n": n, "dim": DIM, "k": K, "leaf_size": leaf, "traversal_variant": variant,
-                       "parallelism": f"replicas x{ws}",
-                       "l2": "working set per step ~1.2 GB > 129 MB L2 (no explicit flush)"},
+            "config": {"workload": WORKLOAD, "n": n, "dim": DIM, "k": K, "parallelism": f"replicas x{ws}",
+                       "l2": L2_NOTE},
+            "launch": {"leaf_size": leaf, "traversal_variant": variant},
             "build_ms": build_ms, "knn_ms": query_ms, "knn_mqps": n / (query_ms / 1e3) / 1e6,
             "build_roofline": hbm_roofline(n * BUILD_BYTES_PER_POINT, build_ms, BUILD_BYTES_MODEL),
             "roofline": roofline, "gpu_launches": launches, "e2e": e2e, "graph_step": graph_rec,
