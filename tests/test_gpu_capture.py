@@ -25,6 +25,7 @@ def api():
 
 
 def _eager(api, x, q, k, leaf):
+    """The same calls made eagerly (also warms up the library outside any capture)."""
     t = api.pg_tree_build(x, leaf)
     out = api.pg_knn(t, None, k) + api.pg_knn(t, q, k)
     info = t.info()
@@ -33,15 +34,18 @@ def _eager(api, x, q, k, leaf):
 
 
 def _data(kind, n, seed):
+    if kind == "gmm7":
+        return synth.gmm(n, 7, seed)
     return synth.uniform(n, 3, seed) if kind == "uniform" else synth.gmm(n, 3, seed)
 
 
 # 25M points: the level lists can exceed the one-block head's 16384 slots, so
 # the captured loop uses classify + device-wide scans + link
 @pytest.mark.parametrize("kind,n,m,leaf", [("uniform", 300_000, 20_000, 16), ("gmm", 200_000, 10_000, 48),
-                                           ("uniform", 2_000, 5_000, 8), ("uniform", 25_000_000, 100_000, 48)])
+                                           ("uniform", 2_000, 5_000, 8), ("uniform", 25_000_000, 100_000, 48),
+                                           ("gmm7", 200_000, 20_000, 64)])
 def test_captured_build_and_knn_replays_exactly(api, kind, n, m, leaf):
-    k = 10
+    k = 16 if kind == "gmm7" else 10   # 7D with k = 16: the automatic traversal is warp per query
     dev = torch.device("cuda:0")
     x = torch.from_numpy(_data(kind, n, 31)).to(dev)
     q = torch.from_numpy(_data(kind, m, 32)).to(dev)
