@@ -1037,8 +1037,16 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
     }
     int hctl[CTL_WORDS] = {0};
     int level = 0;
+    // With a finisher, every segment of a level list is a child of a split
+    // segment of more than fin_max points: that bounds the list, so the
+    // one-block head serves every level of most builds.
+    const int64_t S_bound = (rule == PG_SPLIT_SPATIAL && fin_max > 0)
+                                ? std::min<int64_t>(seg_cap, 2 * (n / (fin_max + 1)) + 2) : seg_cap;
+    // The end flag is read from the expected depth on, then every 2, then 4
+    // levels (levels enqueued after the end do nothing).
+    int next_check = est - 1, stride = 1;
     for (; level <= PG_DEPTH_CAP + 1; ++level) {
-        const int S_max = (int)std::min<int64_t>((int64_t)1 << std::min(level, 30), seg_cap);
+        const int S_max = (int)std::min<int64_t>((int64_t)1 << std::min(level, 30), S_bound);
         PG_TRY(level_segments<DC>(S_max, ctl, cur, nxt, leaf, fin_max, split_flag, split_rank, sdim, sval, fin_flag,
                                   fin_rank, fin, t->nodes, t->split_dim, t->split_val, t->node_range, t->parent,
                                   nullptr, 0, nullptr, s));
@@ -1083,9 +1091,11 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
         std::swap(P, Q);
         std::swap(seg_of, seg_of_nx);
         std::swap(cur, nxt);
-        if (level + 1 >= est) {
+        if (level >= next_check || level == PG_DEPTH_CAP + 1) {
             PG_TRY(read_small(hctl, ctl, sizeof(hctl), s));
             if (hctl[CTL_DONE]) break;
+            stride = std::min(2 * stride, 4);
+            next_check = level + stride;
         }
     }
     if (!hctl[CTL_DONE]) return fail(PG_ECUDA, "tree build: level count exceeded the depth cap");
