@@ -395,7 +395,8 @@ pg_status refresh_forest(const pg_bdl *cb) {
     std::vector<std::pair<int64_t, pg_tree *>> order;
     for (int i = 0; i < 64; ++i)
         if (b->slot[i] && b->slot[i]->live > 0) order.push_back({b->slot[i]->live, b->slot[i]});
-    std::sort(order.begin(), order.end(), [](auto &x, auto &y) { return x.first > y.first; });
+    // largest first (the first of equals in slot order: the tree pg_bdl_knn orders queries by)
+    std::stable_sort(order.begin(), order.end(), [](auto &x, auto &y) { return x.first > y.first; });
     for (auto &o : order) d.push_back(tree_desc(o.second));
     if (b->buffer && b->buffer_live > 0) d.push_back(tree_desc(b->buffer));
     if ((int)d.size() > b->forest_cap) {
@@ -472,18 +473,19 @@ pg_status pg_bdl_knn_ex(const pg_bdl *b, const float *queries, int64_t m, int k,
     if (m > 0 && (!queries || !out_idx || !out_dist)) return fail(PG_EINVAL, "pg_bdl_knn: NULL pointer");
     if (m == 0) return PG_OK;
     PG_TRY(refresh_forest(b));
-    // order the queries by the leaves of the largest tree
+    // order the queries by the leaves of the largest tree (the forest's first
+    // descriptor), where the search then starts from each query's leaf
     const pg_tree *big = nullptr;
     for (int i = 0; i < 64; ++i)
         if (b->slot[i] && b->slot[i]->live > 0 && (!big || b->slot[i]->live > big->live)) big = b->slot[i];
     Scratch ord;
     const bool sorted = big && m >= kOrderMinQueries;
     if (sorted) {
-        PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)m, b->s));
-        PG_TRY(query_order(big, queries, m, b->dim, ord.as<int32_t>(), b->s));
+        PG_TRY(ord.alloc(sizeof(int32_t) * (size_t)(2 * m), b->s));
+        PG_TRY(query_order(big, queries, m, b->dim, ord.as<int32_t>(), b->s, ord.as<int32_t>() + m));
     }
-    return knn_launch(b->forest, b->forest_n, b->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr, nullptr,
-                      m, b->dim, k, out_idx, out_dist, variant, b->s);
+    return knn_launch(b->forest, b->forest_n, b->dc, queries, nullptr, sorted ? ord.as<int32_t>() : nullptr,
+                      sorted ? ord.as<int32_t>() + m : nullptr, m, b->dim, k, out_idx, out_dist, variant, b->s);
 }
 
 pg_status pg_bdl_size(const pg_bdl *b, int64_t *live) {

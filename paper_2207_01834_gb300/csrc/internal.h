@@ -111,10 +111,11 @@ pg_status tree_sync_meta(pg_tree *t);
 // is the entry's id; otherwise queries are row-major m*dim floats.
 // order (may be NULL): processing order of the queries (a permutation of
 // 0..m-1 that puts queries of the same leaf next to each other).
-// start_leaf (may be NULL): per processing position, the bucket position of
-// the leaf the query falls in; traversals that search from the bottom start
-// there.  self_bucket or start_leaf may be given only with ntrees == 1 and a
-// tree that has its parent links (parent, leaf_parent).
+// start_leaf (may be NULL): per processing position, the bucket position in
+// tree 0 of the leaf the query falls in; traversals that search from the
+// bottom start there and then search the other trees from their roots.
+// self_bucket may be given only with ntrees == 1; tree 0 must have its
+// parent links (parent, leaf_parent) when either is given.
 // variant: a PG_KNN_* traversal, or PG_KNN_AUTO for the automatic choice.
 pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float *queries,
                      const float4 *self_bucket, const int32_t *order, const int32_t *start_leaf, int64_t m,

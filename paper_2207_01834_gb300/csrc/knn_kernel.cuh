@@ -429,7 +429,7 @@ enum WwMode : int {
     WW_ANY = 0,     // decided per launch: the cases below, by their conditions
     WW_TOP = 1,     // every tree from its root (forests; queries without a start leaf)
     WW_SELF = 2,    // all-kNN: the query is bucket entry pos of the single tree
-    WW_START = 3,   // separate queries of a single tree from start_leaf[pos]
+    WW_START = 3,   // separate queries from start_leaf[pos] in tree 0, then the other trees from their roots
 };
 
 template <int DC, int KC, bool COUNT = false, int MODE = WW_ANY>
@@ -464,12 +464,13 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
     unsigned nrec = 0, cand = 0;
     bool bottom = MODE == WW_SELF || MODE == WW_START;
     if (MODE == WW_ANY)
-        bottom = (self_bucket || start_leaf) && ntrees == 1 && trees[0].leaf_parent && trees[0].parent;
+        bottom = (self ? ntrees == 1 : start_leaf != nullptr) && trees[0].leaf_parent && trees[0].parent;
+    // from the start leaf in tree 0 (all-kNN: the query's own entry), then the
+    // other trees of a forest from their roots with the k-list tree 0 left
     if (bottom)
         search_self_ww<DC, KC, COUNT>(trees[0], self ? pos : (valid ? (int64_t)start_leaf[pos] : 0), q, dim, valid,
                                       L, nrec, cand);
-    else
-        for (int t = 0; t < ntrees; ++t) search_tree_ww<DC, KC, true, COUNT>(trees[t], q, valid, L, nrec, cand);
+    for (int t = bottom ? 1 : 0; t < ntrees; ++t) search_tree_ww<DC, KC, true, COUNT>(trees[t], q, valid, L, nrec, cand);
     if (COUNT) {
         unsigned long long a = nrec, b = cand;
 #pragma unroll

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(WQ_THREADS) k_knn_warp(const TreeDesc *__restr
     WarpList<KC> L;
     L.init(k, lane);
     int sp = 0;
-    const bool bottom = (self || start_leaf) && ntrees == 1 && trees[0].leaf_parent && trees[0].parent;
+    const bool bottom = (self ? ntrees == 1 : start_leaf != nullptr) && trees[0].leaf_parent && trees[0].parent;
     if (bottom) {
         const TreeDesc &T = trees[0];
         const int64_t lp = self ? pos : (int64_t)start_leaf[pos];
@@ -312,8 +312,9 @@ __global__ void __launch_bounds__(WQ_THREADS) k_knn_warp(const TreeDesc *__restr
         }
         __syncwarp();
         wq_drain<DC, KC>(S, w, sp, T, q, L, lane);
-    } else {
-        for (int t = 0; t < ntrees; ++t) {
+    }
+    {   // the other trees of a forest (all of them without a start leaf), each from its root
+        for (int t = bottom ? 1 : 0; t < ntrees; ++t) {
             const TreeDesc &T = trees[t];
             if (T.root_cnt < 0) continue;
             float rlo[DC], rhi[DC];
