@@ -441,7 +441,33 @@ def k_sweep(api, torch, dev, timed, out):
         del x, q, top_i, top_d
 
 
-EXTRAS = ("2d", "graph_range", "object", "gmm", "bdl", "ksweep")
+def large_k(api, torch, dev, timed, out):
+    """Large k on 3D uniform data (2,000,000 points, leaf 32): separate
+    queries (1,000,000) and all-kNN, k = 32 and 64, with the k-list in
+    registers (postponed leaves), as a shared-memory heap, and warp per
+    query; every variant's answer must be the same bits."""
+    from paper_2207_01834_gb300 import synth
+
+    pts = torch.from_numpy(synth.uniform(2_000_000, 3, synth.BASE_SEED + 60)).to(dev)
+    q = torch.from_numpy(synth.uniform(1_000_000, 3, synth.BASE_SEED + 61)).to(dev)
+    t = api.pg_tree_build(pts, 32)
+    names = {api.KNN_POSTPONED: "postponed_registers", api.KNN_POSTPONED_HEAP: "postponed_heap",
+             api.KNN_WARP: "warp"}
+    for qq, kind in ((q, "1mq"), (None, "all")):
+        for k in (32, 64):
+            ref = api.pg_knn(t, qq, k, variant=api.KNN_POSTPONED)
+            rec, same = {}, True
+            for v, nm in names.items():
+                rec[f"{nm}_ms"] = timed(lambda: api.pg_knn(t, qq, k, variant=v))
+                got = api.pg_knn(t, qq, k, variant=v)
+                same = same and bool(torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]))
+            rec["auto_variant"] = api.pg_knn_tune_get(3, k, qq is None)
+            rec["variants_agree_bitwise"] = same
+            out[f"large_k_3d_uniform_2m_{kind}_k{k}"] = rec
+    t.free()
+
+
+EXTRAS = ("2d", "graph_range", "object", "gmm", "bdl", "ksweep", "largek")
 
 
 def other_configs(api, torch, dev, only=None):
@@ -465,7 +491,7 @@ def other_configs(api, torch, dev, only=None):
 
     out = {}
     sections = {"2d": small_2d, "graph_range": graph_range, "object": object_median, "gmm": gmm_5d_7d,
-                "bdl": bdl_schedule, "ksweep": k_sweep}
+                "bdl": bdl_schedule, "ksweep": k_sweep, "largek": large_k}
     for name in EXTRAS:
         if only is None or name in only:
             sections[name](api, torch, dev, timed, out)
@@ -545,7 +571,7 @@ def gmm_5d_7d(api, torch, dev, timed, out):
         rec = {"build_ms": bms, "knn_ms": qms, "knn_mqps": 1e6 / qms / 1e3, "leaf_size": leaf_d,
                "traversal_variant": var_d,
                "build_roofline": hbm_roofline(2e6 * BUILD_BYTES_PER_POINT, bms, BUILD_BYTES_MODEL)}
-        if var_d == api.KNN_POSTPONED:   # the counting instance exists for this traversal
+        if var_d in (api.KNN_POSTPONED, api.KNN_POSTPONED_HEAP):   # the counting instance walks the same way
             rec["knn_roofline"] = alu_roofline(api, dev, qd, qms, d)
             rec["knn_roofline"]["note"] = "time includes ordering the queries by leaf"
         out[f"{d}d_gmm_2m_1mq_k16"] = rec

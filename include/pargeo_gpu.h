@@ -124,17 +124,25 @@ PG_API pg_status pg_tree_build_split(const float *points, int64_t n, int dim, in
  *                     spread over the lanes (one or two keys each) and
  *                     merged by ballot and shuffle; for higher dimensions
  *                     and large k;
+ *   PG_KNN_POSTPONED_HEAP  PG_KNN_POSTPONED with the k-list of each query
+ *                     kept as a binary max-heap in shared memory (k >= 11:
+ *                     lists of 16, 32 or 64 slots) instead of a sorted
+ *                     register list: an insertion costs about log2(k)
+ *                     steps instead of one per slot; smaller k is
+ *                     PG_KNN_POSTPONED itself;
  *   PG_KNN_AUTO       the calling thread's pg_knn_set_variant choice if set,
  *                     else the tune table entry for the request's dimension
  *                     class, k class and kind (all-kNN or separate queries)
  *                     (pg_knn_tune_set), else PG_KNN_WARP for dimension
- *                     classes from 7 with k >= 16 and PG_KNN_POSTPONED
- *                     otherwise. */
+ *                     classes from 7 with k >= 16 and from 5 with k > 32,
+ *                     PG_KNN_POSTPONED_HEAP for other k > 16 and
+ *                     PG_KNN_POSTPONED otherwise. */
 #define PG_KNN_AUTO 0
 #define PG_KNN_THREAD 1
 #define PG_KNN_PACKET 2
 #define PG_KNN_POSTPONED 3
 #define PG_KNN_WARP 4
+#define PG_KNN_POSTPONED_HEAP 5
 
 /*
  * Exact k-NN of m query points (device, m*dim float32) against the tree's
@@ -284,10 +292,11 @@ PG_API pg_status pg_knn_tune_get(int dim, int k, int all_knn, int *variant);
 
 /*
  * Touched-bytes counters of the traversal (measurement only; no counterpart in
- * the paper).  While enabled (on != 0), every later variant-3 launch in this
- * process runs an instance of the same kernel that also counts, over all its
- * queries, the node records and the bucket entries it loads; the answer is
- * unchanged.  pg_knn_touch_read synchronises the device, returns the counts
+ * the paper).  While enabled (on != 0), every later PG_KNN_POSTPONED or
+ * PG_KNN_POSTPONED_HEAP launch in this process runs an instance of the
+ * postponed-leaf kernel (register k-list; both lists hold the same pairs at
+ * every step, so both walk alike) that also counts, over all its queries, the
+ * node records and the bucket entries it loads; the answer is unchanged.  pg_knn_touch_read synchronises the device, returns the counts
  * accumulated since the last read (zeros if nothing was counted) and resets
  * them.  Bytes: node_records * 16 * (DC + 1), bucket_entries * 16 *
  * ceil((DC + 1) / 4), DC the dimension class.  The counters live on the device

@@ -15,8 +15,8 @@ from .build import LIB
 PG_OK, PG_EINVAL, PG_ENOMEM, PG_ECUDA, PG_ETIMEOUT, PG_EUNSUPPORTED = range(6)
 STATUS_NAMES = {0: "PG_OK", 1: "PG_EINVAL", 2: "PG_ENOMEM", 3: "PG_ECUDA", 4: "PG_ETIMEOUT",
                 5: "PG_EUNSUPPORTED"}
-KNN_AUTO, KNN_THREAD, KNN_PACKET, KNN_POSTPONED, KNN_WARP = 0, 1, 2, 3, 4
-KNN_VARIANTS = (KNN_THREAD, KNN_PACKET, KNN_POSTPONED, KNN_WARP)
+KNN_AUTO, KNN_THREAD, KNN_PACKET, KNN_POSTPONED, KNN_WARP, KNN_POSTPONED_HEAP = 0, 1, 2, 3, 4, 5
+KNN_VARIANTS = (KNN_THREAD, KNN_PACKET, KNN_POSTPONED, KNN_WARP, KNN_POSTPONED_HEAP)
 MAX_DIM = 16
 MAX_K = 64
 MAX_LEAF = 256

@@ -13,11 +13,12 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import KNN_AUTO, KNN_PACKET, KNN_POSTPONED, KNN_THREAD, KNN_VARIANTS, KNN_WARP, PgError, TreeInfo, call
+from ._lib import (KNN_AUTO, KNN_PACKET, KNN_POSTPONED, KNN_POSTPONED_HEAP, KNN_THREAD, KNN_VARIANTS, KNN_WARP, PgError,
+                   TreeInfo, call)
 
 __all__ = ["Tree", "BDL", "PgError", "pg_tree_build", "pg_tree_build_split", "pg_knn", "pg_tree_free", "pg_tree_info",
            "pg_tree_export", "pg_knn_graph", "pg_range", "pg_knn_set_variant", "pg_knn_tune_set", "pg_knn_tune_get", "KNN_AUTO", "KNN_THREAD", "KNN_PACKET",
-           "KNN_POSTPONED", "KNN_WARP", "KNN_VARIANTS", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
+           "KNN_POSTPONED", "KNN_WARP", "KNN_POSTPONED_HEAP", "KNN_VARIANTS", "pg_knn_touch_enable", "pg_knn_touch_read", "pg_bdl_create", "pg_bdl_insert", "pg_bdl_erase", "pg_bdl_knn", "pg_bdl_size",
            "pg_bdl_structure", "pg_bdl_slot_of", "pg_bdl_free", "pg_knn_backward", "pg_knn_backward_noalloc",
            "pg_batched_chamfer",
            "pg_batched_chamfer_backward", "launch_count", "profile_enable", "profile_read", "version",
@@ -206,7 +207,7 @@ def pg_knn_tune_get(dim: int, k: int, all_knn: bool) -> int:
 
 
 def pg_knn_touch_enable(on: bool = True) -> None:
-    """Count node records and bucket entries loaded by later variant-3 launches."""
+    """Count node records and bucket entries loaded by later postponed-leaf launches (variants 3 and 5)."""
     call("pg_knn_touch_enable", 1 if on else 0)
 
 

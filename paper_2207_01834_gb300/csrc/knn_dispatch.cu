@@ -60,14 +60,20 @@ std::atomic<bool> g_touch{false};                      // count touched records 
 unsigned long long *g_touch_dev = nullptr;             // [node records, bucket entries] (one device)
 
 // Built-in choice when nothing else is set: the postponed-leaf traversal,
-// the fastest measured variant on 2D-5D all-kNN and separate queries; warp
-// per query from 7 dimensions and k >= 16 (7D clustered, 1M queries: k = 16
-// 28.5 against 30.7 ms, k = 64 55.8 against 121 ms at each one's best leaf).
-int default_variant(int dc, int k, bool /*self*/) { return dc >= 7 && k >= 16 ? PG_KNN_WARP : PG_KNN_POSTPONED; }
+// the fastest measured variant on 2D-5D all-kNN and separate queries, with
+// its k-list as a shared-memory heap for k > 16 (3D uniform, 2M points, 1M
+// queries, k = 64: 7.2 against 10.2 ms); warp per query from 7 dimensions
+// and k >= 16 (7D clustered, 1M queries: k = 16 28.3 against 32.9 ms, k = 64
+// 55.6 against 107 ms) and from 5 dimensions and k > 32 (5D clustered, k = 64:
+// 30.3 against 32.8 ms; all-kNN even).
+int default_variant(int dc, int k, bool /*self*/) {
+    if ((dc >= 7 && k >= 16) || (dc >= 5 && k > 32)) return PG_KNN_WARP;
+    return k > 16 ? PG_KNN_POSTPONED_HEAP : PG_KNN_POSTPONED;
+}
 
 }  // namespace
 
-bool valid_variant(int v) { return v >= PG_KNN_AUTO && v <= PG_KNN_WARP; }
+bool valid_variant(int v) { return v >= PG_KNN_AUTO && v <= PG_KNN_POSTPONED_HEAP; }
 
 int resolve_variant(int requested, int dc, int k, bool self) {
     if (requested != PG_KNN_AUTO) return requested;
@@ -82,7 +88,7 @@ pg_status knn_launch(const TreeDesc *trees_dev, int ntrees, int dc, const float 
     if (m == 0) return PG_OK;
     if (!valid_variant(requested)) return fail(PG_EINVAL, "k-NN: unknown traversal variant");
     int variant = resolve_variant(requested, dc, k, self_bucket != nullptr);
-    if (g_touch.load() && variant == PG_KNN_POSTPONED) {
+    if (g_touch.load() && (variant == PG_KNN_POSTPONED || variant == PG_KNN_POSTPONED_HEAP)) {
         if (!g_touch_dev) {
             PG_CUDA(cudaMalloc(&g_touch_dev, 2 * sizeof(unsigned long long)));
             PG_CUDA(cudaMemset(g_touch_dev, 0, 2 * sizeof(unsigned long long)));

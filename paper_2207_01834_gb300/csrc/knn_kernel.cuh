@@ -81,6 +81,69 @@ struct KList {
     }
 };
 
+// The same k best pairs as a binary max-heap in shared memory, for large k:
+// an insertion replaces the root (the k-th pair) and sifts the new key down,
+// about log2(k) levels of two loads and one store instead of KC compare-and-
+// select steps on registers, and the list costs no registers.  Slot j of
+// thread t is word j * KNN_THREADS + t, so the 32 lanes of a warp always hit
+// 32 different bank pairs, whatever slots they are at.  The root is also
+// kept in a register (`top`) for the pruning tests.  Only the set of keys
+// matters until the end, where a heapsort writes them out ascending: the
+// answer is the same k smallest (distance, id) pairs as with KList.
+template <int KC>
+struct SmemHeap {
+    static constexpr int LEVELS = KC >= 64 ? 7 : KC >= 32 ? 6 : KC >= 16 ? 5 : KC >= 8 ? 4 : KC >= 4 ? 3 : KC >= 2 ? 2 : 1;   // floor(log2 KC) + 1
+    unsigned long long *h;
+    unsigned long long top;
+    int k;
+
+    // base: KC * KNN_THREADS words of shared memory for the thread block
+    __device__ __forceinline__ void init(unsigned long long *base, int k_) {
+        h = base + threadIdx.x;
+        k = k_;
+        for (int j = 0; j < k; ++j) h[j * KNN_THREADS] = PAD_KEY;
+        top = PAD_KEY;
+    }
+    __device__ __forceinline__ float kth() const { return __uint_as_float((unsigned)(top >> 32)); }
+    __device__ __forceinline__ unsigned long long kth_key() const { return top; }
+
+    // Sift key kx down from slot i of a heap of n slots; every lane of the
+    // warp runs the same LEVELS steps, lanes without `act` change nothing.
+    __device__ __forceinline__ void sift(unsigned long long kx, int i, int n, bool act) {
+#pragma unroll
+        for (int l = 0; l < LEVELS; ++l) {
+            const int c = 2 * i + 1;
+            const bool has = act && c < n;
+            const unsigned long long a = has ? h[c * KNN_THREADS] : 0ull;
+            const unsigned long long b = has && c + 1 < n ? h[(c + 1) * KNN_THREADS] : 0ull;
+            const bool right = b > a;
+            const unsigned long long m = right ? b : a;
+            const bool down = has && m > kx;
+            if (act) h[i * KNN_THREADS] = down ? m : kx;
+            act = down;
+            i = right ? c + 1 : c;
+        }
+    }
+    __device__ __forceinline__ void offer_pred(float x, unsigned ix, bool ok) {
+        const unsigned long long kx = pair_key(x, ix);
+        ok = ok && kx < top;
+        sift(kx, 0, k, ok);
+        if (ok) top = h[0];
+    }
+    __device__ __forceinline__ void offer(float x, unsigned ix) {
+        if (pair_key(x, ix) < top) offer_pred(x, ix, true);
+    }
+    // Heapsort: the largest goes last.  The heap ends in no particular state.
+    __device__ __forceinline__ void write_sorted(int32_t *oi, float *od) {
+        for (int n = k; n > 0; --n) {
+            const unsigned long long r = h[0];
+            oi[n - 1] = (unsigned)r == DEAD_ID ? -1 : (int32_t)(unsigned)r;
+            od[n - 1] = __uint_as_float((unsigned)(r >> 32));
+            if (n > 1) sift(h[(n - 1) * KNN_THREADS], 0, n - 1, true);
+        }
+    }
+};
+
 // NC: read through the non-coherent read-only path (data constant for the
 // whole kernel); false for trees built earlier in the same kernel.
 template <bool NC>
@@ -198,9 +261,9 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
 // insertions then run converged (as many rounds as the busiest lane needs).
 // Each lane's pruning uses only its own k-th distance, so the answer is the
 // same exact k-NN as the other variants.
-template <int DC, int KC, bool NC = true, bool COUNT = false>
+template <int DC, int KC, bool NC = true, bool COUNT = false, class LT = KList<KC>>
 __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict__ bucket, int lref, int lcnt,
-                                                        const float *q, KList<KC> &L, unsigned &cand) {
+                                                        const float *q, LT &L, unsigned &cand) {
     const int maxc = __reduce_max_sync(0xffffffffu, lcnt);
     for (int base = 0; base < maxc; base += 32) {
         const int n = min(32, maxc - base);
@@ -232,8 +295,8 @@ __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict
 
 // COUNT: also count, per lane, the node records and bucket entries it loads
 // (the touched-bytes model of the traversal; a separate instantiation).
-template <int DC, int KC, bool NC = true, bool COUNT = false>
-__device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q, bool valid, KList<KC> &L,
+template <int DC, int KC, bool NC = true, bool COUNT = false, class LT = KList<KC>>
+__device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q, bool valid, LT &L,
                                                unsigned &nrec, unsigned &cand) {
     constexpr int NW = node_w(DC);
     int s_ref[KNN_STACK], s_cnt[KNN_STACK];
@@ -311,9 +374,9 @@ __device__ __forceinline__ void search_tree_ww(const TreeDesc &T, const float *q
 // that already holds a leaf keeps walking while some other lane of the warp
 // still looks for one, so fewer lanes idle in the node phase.  A queued leaf
 // is tested again against the k-th distance when it is taken.
-template <int DC, int KC, bool COUNT = false>
+template <int DC, int KC, bool COUNT = false, class LT = KList<KC>>
 __device__ __forceinline__ void search_self_ww(const TreeDesc &T, int64_t pos, const float *q, int dim, bool valid,
-                                               KList<KC> &L, unsigned &nrec, unsigned &cand) {
+                                               LT &L, unsigned &nrec, unsigned &cand) {
     constexpr int NW = node_w(DC);
     int s_ref[KNN_STACK], s_cnt[KNN_STACK];
     float s_d[KNN_STACK];
@@ -432,7 +495,14 @@ enum WwMode : int {
     WW_START = 3,   // separate queries from start_leaf[pos] in tree 0, then the other trees from their roots
 };
 
-template <int DC, int KC, bool COUNT = false, int MODE = WW_ANY>
+// The k-list of the postponed-leaf kernel: registers, or (HEAP) a max-heap in
+// KC * KNN_THREADS words of dynamic shared memory.
+template <bool HEAP, int KC>
+struct WwList { using type = KList<KC>; };
+template <int KC>
+struct WwList<true, KC> { using type = SmemHeap<KC>; };
+
+template <int DC, int KC, bool COUNT = false, int MODE = WW_ANY, bool HEAP = false>
 __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restrict__ trees, int ntrees,
                                                         const float *__restrict__ queries,
                                                         const float4 *__restrict__ self_bucket,
@@ -459,8 +529,13 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
             for (int c = 0; c < DC; ++c) q[c] = c < dim ? queries[row * dim + c] : 0.f;
         }
     }
-    KList<KC> L;
-    L.init(k);
+    typename WwList<HEAP, KC>::type L;
+    if constexpr (HEAP) {
+        extern __shared__ unsigned long long ww_heap[];
+        L.init(ww_heap, k);
+    } else {
+        L.init(k);
+    }
     unsigned nrec = 0, cand = 0;
     bool bottom = MODE == WW_SELF || MODE == WW_START;
     if (MODE == WW_ANY)
@@ -486,12 +561,16 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn_ww(const TreeDesc *__restri
     if (!valid) return;
     int32_t *oi = out_idx + row * k;
     float *od = out_dist + row * k;
+    if constexpr (HEAP) {
+        L.write_sorted(oi, od);
+    } else {
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        if (j >= KC - k) {
-            const int o = j - (KC - k);
-            oi[o] = L.idx(j) == DEAD_ID ? -1 : (int32_t)L.idx(j);
-            od[o] = L.dist(j);
+        for (int j = 0; j < KC; ++j) {
+            if (j >= KC - k) {
+                const int o = j - (KC - k);
+                oi[o] = L.idx(j) == DEAD_ID ? -1 : (int32_t)L.idx(j);
+                od[o] = L.dist(j);
+            }
         }
     }
 }
@@ -834,28 +913,64 @@ __global__ void __launch_bounds__(KNN_THREADS) k_knn(const TreeDesc *__restrict_
     }
 }
 
+// PG_KNN_POSTPONED_HEAP: the postponed-leaf kernel with its k-list as a
+// shared-memory heap for list capacities from 16; smaller lists stay in
+// registers (the PG_KNN_POSTPONED instances).
+template <int DC, int KC, int MODE>
+cudaError_t launch_knn_ww_mode(const TreeDesc *trees, int ntrees, const float *queries, const float4 *self_bucket,
+                               const int32_t *order, const int32_t *start_leaf, int64_t m, int dim, int k,
+                               int32_t *out_idx, float *out_dist, bool heap, cudaStream_t s) {
+    constexpr bool CAN_HEAP = KC >= 16;
+    if (CAN_HEAP && heap) {
+        constexpr int smem = KC * KNN_THREADS * (int)sizeof(unsigned long long);
+        const cudaError_t e = cudaFuncSetAttribute(k_knn_ww<DC, KC, false, MODE, CAN_HEAP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        k_knn_ww<DC, KC, false, MODE, CAN_HEAP><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, smem, s>>>(
+            trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);
+    } else {
+        k_knn_ww<DC, KC, false, MODE><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(
+            trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);
+    }
+    return cudaSuccess;
+}
+
+// The start mode of a postponed-leaf launch: all-kNN from the own entry,
+// separate queries from their start leaves, else every tree from its root.
+template <int DC, int KC>
+cudaError_t launch_knn_ww(const TreeDesc *trees, int ntrees, const float *queries, const float4 *self_bucket,
+                          const int32_t *order, const int32_t *start_leaf, int64_t m, int dim, int k,
+                          int32_t *out_idx, float *out_dist, bool heap, cudaStream_t s) {
+    if (self_bucket)
+        return launch_knn_ww_mode<DC, KC, WW_SELF>(trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k,
+                                                   out_idx, out_dist, heap, s);
+    if (start_leaf)
+        return launch_knn_ww_mode<DC, KC, WW_START>(trees, ntrees, queries, self_bucket, order, start_leaf, m, dim,
+                                                    k, out_idx, out_dist, heap, s);
+    return launch_knn_ww_mode<DC, KC, WW_TOP>(trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k,
+                                              out_idx, out_dist, heap, s);
+}
+
 }  // namespace pg
 
 #include "knn_warp.cuh"
 
 // Host launcher for one dimension class: picks the list capacity KC >= k and
 // the traversal kernel for the resolved variant (PG_KNN_THREAD,
-// PG_KNN_POSTPONED, PG_KNN_WARP, the counting instance, else warp packets).
+// PG_KNN_POSTPONED[_HEAP], PG_KNN_WARP, the counting instance, else warp
+// packets).
 #define PG_KNN_CASE(DCN, KCN)                                                                              \
     case KCN:                                                                                              \
         if (variant == PG_KNN_THREAD)                                                                      \
             k_knn<DCN, KCN><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(trees, ntrees, queries,      \
                                                                                self_bucket, m, dim, k,     \
                                                                                out_idx, out_dist);         \
-        else if (variant == PG_KNN_POSTPONED && self_bucket)                                               \
-            k_knn_ww<DCN, KCN, false, WW_SELF><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(         \
-                trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);     \
-        else if (variant == PG_KNN_POSTPONED && start_leaf)                                                \
-            k_knn_ww<DCN, KCN, false, WW_START><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(        \
-                trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);     \
-        else if (variant == PG_KNN_POSTPONED)                                                              \
-            k_knn_ww<DCN, KCN, false, WW_TOP><<<ceil_div_i(m, KNN_THREADS), KNN_THREADS, 0, s>>>(          \
-                trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k, out_idx, out_dist);     \
+        else if (variant == PG_KNN_POSTPONED || variant == PG_KNN_POSTPONED_HEAP) {                        \
+            if (launch_knn_ww<DCN, KCN>(trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k,   \
+                                        out_idx, out_dist, variant == PG_KNN_POSTPONED_HEAP, s) !=          \
+                cudaSuccess)                                                                               \
+                return fail(PG_ECUDA, "k-NN: shared-memory size of the heap traversal");                  \
+        }                                                                                                  \
         else if (variant == PG_KNN_WARP)                                                                   \
             launch_knn_warp<DCN, KCN>(trees, ntrees, queries, self_bucket, order, start_leaf, m, dim, k,     \
                                       out_idx, out_dist, s);                                               \

@@ -184,11 +184,13 @@ def test_error_text_is_per_thread(lib):
 
 def test_automatic_traversal_choice_without_a_device(lib):
     """PG_KNN_AUTO resolves on the host: the built-in choice is warp per query
-    from dimension class 7 with k >= 16, postponed leaves otherwise; a tune
-    table entry overrides it for its (dimension class, k class, kind)."""
+    from dimension class 7 with k >= 16 and from class 5 with k > 32,
+    postponed leaves otherwise, with the shared-memory heap for k > 16; a
+    tune table entry overrides it for its (dimension class, k class, kind)."""
     v = C.c_int(-1)
     for dim, k, all_knn, want in [(3, 10, 1, 3), (5, 16, 0, 3), (7, 15, 0, 3), (7, 16, 0, 4), (9, 64, 1, 4),
-                                  (16, 32, 0, 4), (2, 1, 1, 3)]:
+                                  (16, 32, 0, 4), (2, 1, 1, 3), (3, 17, 1, 5), (3, 64, 0, 5), (4, 64, 1, 5),
+                                  (5, 32, 0, 5), (5, 33, 0, 4), (6, 64, 1, 4)]:
         assert lib.pg_knn_tune_get(dim, k, all_knn, C.byref(v)) == 0
         assert v.value == want, (dim, k, all_knn, v.value)
     try:
@@ -199,4 +201,4 @@ def test_automatic_traversal_choice_without_a_device(lib):
         assert v.value == 4
     finally:
         lib.pg_knn_tune_set(7, 16, 0, 0)
-    assert lib.pg_knn_tune_set(3, 10, 1, 5) != 0     # not a traversal
+    assert lib.pg_knn_tune_set(3, 10, 1, 6) != 0     # not a traversal

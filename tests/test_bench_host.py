@@ -78,9 +78,10 @@ def _standins(monkeypatch):
                                   equal=lambda a, b: np.array_equal(a.a, b.a))
     api = types.SimpleNamespace(
         pg_tree_build=lambda x, leaf: _Tree(), pg_tree_build_split=lambda x, leaf, rule: _Tree(), SPLIT_OBJECT=1,
-        pg_knn=lambda t, q, k, **kw: None, pg_knn_graph=lambda t, k: _Arr(np.zeros((5, 2))),
+        pg_knn=lambda t, q, k, **kw: (_Arr(np.zeros((4, k), np.int32)), _Arr(np.zeros((4, k), np.float32))),
+        pg_knn_graph=lambda t, k: _Arr(np.zeros((5, 2))), pg_knn_tune_get=lambda dim, k, all_knn: 5,
         pg_range=lambda t, q, r: (_Arr(np.zeros(7)), _Arr(np.zeros(3))),
-        BDL=_Forest, KNN_POSTPONED=3, pg_knn_touch_enable=lambda on: None, pg_knn_touch_read=lambda: (10, 100))
+        BDL=_Forest, KNN_POSTPONED=3, KNN_WARP=4, KNN_POSTPONED_HEAP=5, pg_knn_touch_enable=lambda on: None, pg_knn_touch_read=lambda: (10, 100))
     monkeypatch.setattr(autotune, "best_config", lambda pts, k, queries=None: (32, 3))
     return api, torch
 
@@ -91,7 +92,9 @@ def test_other_workloads_all_sections(monkeypatch):
     assert sorted(out) == sorted(["2d_20k_k5", "knn_graph_2d_10m_k10", "range_2d_10m_all_r_for_10",
                                   "object_median_3d_10m_k10", "5d_gmm_2m_1mq_k16", "7d_gmm_2m_1mq_k16",
                                   "bdl_3d_4m_schedule", "k_sweep_2d_gmm_10m_5pct_inserts",
-                                  "k_sweep_7d_uniform_10m_5pct_inserts"])
+                                  "k_sweep_7d_uniform_10m_5pct_inserts"] +
+                                 [f"large_k_3d_uniform_2m_{kind}_k{k}" for kind in ("1mq", "all") for k in (32, 64)])
+    assert all(out[f"large_k_3d_uniform_2m_all_k{k}"]["variants_agree_bitwise"] for k in (32, 64))
     for name in ("k_sweep_2d_gmm_10m_5pct_inserts", "k_sweep_7d_uniform_10m_5pct_inserts"):
         assert out[name]["k"] == list(range(2, 12)) and out[name]["prefix_consistent_with_k11"]
     for key in ("insert_roofline", "erase_roofline", "forest_knn_roofline"):

@@ -192,6 +192,9 @@ def test_forest_variants_agree_bitwise(api, m):
     outs = [f.knn(_cuda(q), 10, variant=v) for v in api.KNN_VARIANTS]
     for got in outs[1:]:
         assert torch.equal(got[0], outs[0][0]) and torch.equal(got[1], outs[0][1])
+    wide = [f.knn(_cuda(q), 24, variant=v) for v in api.KNN_VARIANTS]   # lists of 32 slots
+    for got in wide[1:]:
+        assert torch.equal(got[0], wide[0][0]) and torch.equal(got[1], wide[0][1])
     pts, ids = model.live_arrays()
     o_idx, o_dist = oracle.knn(pts, q, 10, ids=ids, nthreads=0)
     compare_knn(outs[-1][0].cpu().numpy(), outs[-1][1].cpu().numpy(), o_idx, o_dist, pts, q, ids=ids)

@@ -41,11 +41,13 @@ def _data(kind, n, seed):
 
 # 25M points: the level lists can exceed the one-block head's 16384 slots, so
 # the captured loop uses classify + device-wide scans + link
-@pytest.mark.parametrize("kind,n,m,leaf", [("uniform", 300_000, 20_000, 16), ("gmm", 200_000, 10_000, 48),
-                                           ("uniform", 2_000, 5_000, 8), ("uniform", 25_000_000, 100_000, 48),
-                                           ("gmm7", 200_000, 20_000, 64)])
-def test_captured_build_and_knn_replays_exactly(api, kind, n, m, leaf):
-    k = 16 if kind == "gmm7" else 10   # 7D with k = 16: the automatic traversal is warp per query
+# 7D with k = 16: the automatic traversal is warp per query; 3D with k = 40:
+# postponed leaves with the k-list in shared memory
+@pytest.mark.parametrize("kind,n,m,leaf,k", [("uniform", 300_000, 20_000, 16, 10), ("gmm", 200_000, 10_000, 48, 10),
+                                             ("uniform", 2_000, 5_000, 8, 10),
+                                             ("uniform", 25_000_000, 100_000, 48, 10),
+                                             ("gmm7", 200_000, 20_000, 64, 16), ("gmm", 200_000, 20_000, 32, 40)])
+def test_captured_build_and_knn_replays_exactly(api, kind, n, m, leaf, k):
     dev = torch.device("cuda:0")
     x = torch.from_numpy(_data(kind, n, 31)).to(dev)
     q = torch.from_numpy(_data(kind, m, 32)).to(dev)

@@ -23,7 +23,7 @@ def api():
     return a
 
 
-@pytest.fixture(params=[1, 2, 3, 4], ids=["thread", "packet", "postponed", "warp"])
+@pytest.fixture(params=[1, 2, 3, 4, 5], ids=["thread", "packet", "postponed", "warp", "postponed-heap"])
 def variant(api, request):
     """This thread's traversal override for the test's PG_KNN_AUTO calls."""
     api.pg_knn_set_variant(request.param)
@@ -166,20 +166,22 @@ def test_knn_lattice_exact(api, variant):
     assert np.array_equal(dist.cpu().numpy().astype(np.float64), o_dist)
 
 
-def test_knn_duplicates_prefer_small_ids(api, variant):
+@pytest.mark.parametrize("copies", [6, 20])   # 20: a list of 32 slots (a heap for the heap traversal)
+def test_knn_duplicates_prefer_small_ids(api, variant, copies):
     base = synth.uniform(300, 3, 21)
-    pts = np.concatenate([base] * 6)              # 6 copies, ids i, i+300, ...
+    pts = np.concatenate([base] * copies)         # copies, ids i, i+300, ...
     tree = api.pg_tree_build(_cuda(pts), leaf_size=4)
-    idx, dist = api.pg_knn(tree, _cuda(base), 6)
-    want = np.arange(300)[:, None] + 300 * np.arange(6)[None, :]
+    idx, dist = api.pg_knn(tree, _cuda(base), copies)
+    want = np.arange(300)[:, None] + 300 * np.arange(copies)[None, :]
     assert np.array_equal(idx.cpu().numpy(), want)
     assert torch.all(dist == 0)
 
 
-def test_knn_padding(api, variant):
+@pytest.mark.parametrize("k", [10, 40])
+def test_knn_padding(api, variant, k):
     pts = synth.uniform(3, 3, 22)
     tree = api.pg_tree_build(_cuda(pts), leaf_size=16)
-    idx, dist = api.pg_knn(tree, _cuda(synth.uniform(5, 3, 23)), 10)
+    idx, dist = api.pg_knn(tree, _cuda(synth.uniform(5, 3, 23)), k)
     idx = idx.cpu().numpy()
     assert np.all(idx[:, 3:] == -1) and torch.all(torch.isinf(dist[:, 3:]))
     assert np.all(np.sort(idx[:, :3], axis=1) == np.arange(3))
@@ -194,7 +196,7 @@ def test_variants_agree_bitwise(api):
     outs = []
     for v in api.KNN_VARIANTS:
         api.pg_knn_set_variant(v)
-        outs.append(api.pg_knn(tree, _cuda(q), 12) + api.pg_knn(tree, None, 7))
+        outs.append(api.pg_knn(tree, _cuda(q), 12) + api.pg_knn(tree, None, 7) + api.pg_knn(tree, None, 40))
     api.pg_knn_set_variant(0)
     for other in outs[1:]:
         for a, b in zip(outs[0], other):
