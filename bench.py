@@ -50,15 +50,16 @@ def parse():
     # the postponed-leaf traversal; leaf 64 is within 1%); 0 re-tunes at run time
     p.add_argument("--leaf", type=int, default=48, help="leaf size (0: autotuned)")
     p.add_argument("--variant", type=int, default=3,
-                   help="traversal: 0 autotuned, 1 thread per query, 2 warp packets, 3 postponed leaves")
+                   help="traversal: 0 autotuned, 1 thread per query, 2 warp packets, 3 postponed leaves, "
+                        "4 warp per query, 5 postponed leaves with the k-list in shared memory")
     p.add_argument("--n", type=int, default=N_POINTS, help=argparse.SUPPRESS)
     p.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-cpu", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-extras", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--extras-only", default="", metavar="NAMES",
-                   help="time only these other workloads, comma separated: 2d, graph_range, object, gmm, bdl "
-                        "(for profiling)")
+                   help="time only these other workloads, comma separated: 2d, graph_range, object, gmm, bdl, "
+                        "ksweep, largek (for profiling)")
     p.add_argument("--batched-only", type=int, default=0, metavar="K",
                    help="time only the batched Chamfer forward + backward with this k (for profiling)")
     p.add_argument("--profile-launches", action="store_true",

@@ -257,8 +257,10 @@ __device__ __forceinline__ void search_tree(const TreeDesc &T, const float *q, K
 // scan or is finished; only when every lane of the warp is in that state do
 // the lanes scan their leaves together, so leaf work, the bulk of the
 // instructions, runs with the warp converged.  Candidates of a leaf chunk are
-// first tested against the lane's k-th pair into a bit mask, and the
-// insertions then run converged (as many rounds as the busiest lane needs).
+// first tested against the lane's k-th distance into a bit mask (a float
+// compare: a candidate at exactly the k-th distance also passes, and the
+// insertion's full (distance, id) compare decides it), and the insertions
+// then run converged (as many rounds as the busiest lane needs).
 // Each lane's pruning uses only its own k-th distance, so the answer is the
 // same exact k-NN as the other variants.
 template <int DC, int KC, bool NC = true, bool COUNT = false, class LT = KList<KC>>
@@ -268,7 +270,7 @@ __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict
     for (int base = 0; base < maxc; base += 32) {
         const int n = min(32, maxc - base);
         unsigned mask = 0;
-        const unsigned long long kk = L.kth_key();
+        const float kf = L.kth();
         for (int j = 0; j < n; ++j) {
             if (base + j < lcnt) {
                 float p[DC];
@@ -276,7 +278,7 @@ __device__ __forceinline__ void scan_own_leaf_converged(const float4 *__restrict
                 load_point<DC, NC>(bucket, lref + base + j, p, pid);
                 if (COUNT) ++cand;
                 const float dd = sqdist<DC>(q, p);
-                mask |= (pair_key(dd, pid) < kk ? 1u : 0u) << j;
+                mask |= (dd <= kf ? 1u : 0u) << j;
             }
         }
         const int rounds = __reduce_max_sync(0xffffffffu, __popc(mask));
