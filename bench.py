@@ -144,7 +144,7 @@ def kernel_sha(names):
 KNN_SOURCES = ["knn_kernel.cuh", "knn_warp.cuh", "common.cuh", "knn_dc3.cu"]
 
 
-KNN_KERNELS = {1: "k_knn", 2: "k_knn_packet", 3: "k_knn_ww"}
+KNN_KERNELS = {1: "k_knn", 2: "k_knn_packet", 3: "k_knn_ww", 4: "k_knn_warp", 5: "k_knn_ww"}
 
 
 def traffic_record(kernel: str, sha: str, variant: int, leaf: int):
