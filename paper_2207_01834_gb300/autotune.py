@@ -1,7 +1,8 @@
-"""Autotuner for the k-NN path's launch parameters: the tree's leaf size and
-the traversal kernel (thread per query, warp packets, postponed leaves, warp
-per query; the last also places the k-list across the warp's lanes instead
-of one thread's registers), and the leaf size of the batched Chamfer path.
+"""Autotuner for the k-NN path's launch parameters: the tree's leaf size, the
+traversal kernel (thread per query, warp packets, postponed leaves, warp per
+query) and where the k-list lives (one thread's registers, a binary heap in
+shared memory for lists of more than 16 pairs, or spread across a warp's
+lanes with warp per query), and the leaf size of the batched Chamfer path.
 
 It times the candidates on the caller's own data (build + query through the C
 ABI, CUDA events, after a warm-up; the traversal is named per call, so no
@@ -95,6 +96,8 @@ def best_config(x: torch.Tensor, k: int, queries=None, leaves=LEAF_CANDIDATES,
     if key in cache:
         leaf, var = int(cache[key]["leaf"]), int(cache[key]["variant"])
     else:
+        # up to k = 16 the shared-memory heap variant runs the register-list kernel itself
+        variants = [v for v in variants if not (v == api.KNN_POSTPONED_HEAP and k <= 16)] or list(variants)
         times = {(leaf, var): _time_leaf(x, queries, k, leaf, var) for var in variants for leaf in leaves}
         leaf, var = min(times, key=times.get)
         with _lock:

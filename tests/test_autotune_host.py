@@ -33,12 +33,21 @@ def test_picks_the_fastest_and_caches(tuner):
     x = torch.from_numpy(np.zeros((5000, 3), np.float32))
     assert autotune.best_config(x, 10) == (32, 3)
     assert state["tuned"] == [(3, 10, True, 3)]
-    assert len(state["timed"]) == len(autotune.LEAF_CANDIDATES) * len(autotune.VARIANT_CANDIDATES)
-    assert set(v for _, v in state["timed"]) == set(autotune.VARIANT_CANDIDATES)
+    # k <= 16: the shared-memory heap variant is the register-list kernel itself, not timed twice
+    small_k = set(autotune.VARIANT_CANDIDATES) - {autotune.api.KNN_POSTPONED_HEAP}
+    assert len(state["timed"]) == len(autotune.LEAF_CANDIDATES) * len(small_k)
+    assert set(v for _, v in state["timed"]) == small_k
     state["timed"].clear()
     assert autotune.best_config(x, 10, queries=None) == (32, 3)          # from the cache
     assert state["timed"] == [] and state["tuned"][-1] == (3, 10, True, 3)
     assert state["override"] == []                                       # no process-wide side effect
+
+
+def test_large_k_times_the_heap_variant(tuner):
+    autotune, state = tuner
+    x = torch.from_numpy(np.zeros((5000, 3), np.float32))
+    autotune.best_config(x, 32)
+    assert set(v for _, v in state["timed"]) == set(autotune.VARIANT_CANDIDATES)
 
 
 def test_cache_key_separates_workloads(tuner):
