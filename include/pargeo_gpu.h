@@ -327,6 +327,9 @@ PG_API pg_status pg_bdl_create(int dim, int64_t buffer_size, int leaf_size, void
  * highest new slot taking what remains.
  * Points receive consecutive ids in input order, continuing from earlier
  * inserts; out_ids (device, cnt int32, may be NULL) receives them.
+ * All or nothing: every new tree is built before the forest changes, so on
+ * an error (PG_ENOMEM, PG_ECUDA) the forest holds what it held before the
+ * call and the next insert hands out the same ids.
  */
 PG_API pg_status pg_bdl_insert(pg_bdl *bdl, const float *points, int64_t cnt, int32_t *out_ids);
 
@@ -335,7 +338,10 @@ PG_API pg_status pg_bdl_insert(pg_bdl *bdl, const float *points, int64_t cnt, in
  * one of the cnt points (device, cnt*dim float32) is removed from its tree;
  * then every tree left with fewer than half of its capacity is destroyed and
  * its live points are reinserted with Insert_L (the buffer tree is exempt).
- * Points not present are ignored.
+ * Points not present are ignored.  On an error the erase has either removed
+ * nothing or removed every match (queries are exact either way); in the
+ * second case a failed reinsertion leaves the under-full trees in place and
+ * erasing the same points again is harmless.
  */
 PG_API pg_status pg_bdl_erase(pg_bdl *bdl, const float *points, int64_t cnt);
 

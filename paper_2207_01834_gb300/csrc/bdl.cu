@@ -228,26 +228,26 @@ void drop_tree(pg_tree *&t) {
     }
 }
 
-pg_status rebuild_buffer(pg_bdl *b) {
-    Scratch ids;
-    int64_t cnt = 0;
-    PG_TRY(bdl_collect(b, 0, true, ids, &cnt));
-    drop_tree(b->buffer);
-    b->buffer_live = cnt;
-    if (cnt > 0) PG_TRY(new_tree(b, ids.as<int32_t>(), cnt, &b->buffer));
-    return PG_OK;
-}
+// The trees an Insert_L creates, built before the forest changes.
+struct InsertPlan {
+    pg_tree *made[64] = {};
+    pg_tree *buffer = nullptr;   // the rebuilt buffer tree (when buffer_changed)
+    bool buffer_changed = false;
+    int64_t buffer_live = 0;
+    uint64_t F = 0, consumed = 0;
+};
 
-// Insert_L over an id list (device, in pool order).
-pg_status insert_ids(pg_bdl *b, const int32_t *ids, int64_t cnt) {
-    if (cnt <= 0) return PG_OK;
+// Insert_L over an id list (device, in pool order) against the full-tree
+// mask F0: every new tree, and the new buffer tree, is built here; the only
+// state of the forest this changes is the slot code of ids.
+pg_status insert_plan(pg_bdl *b, const int32_t *ids, int64_t cnt, uint64_t F0, InsertPlan &p) {
     const int64_t X = b->X;
     int64_t q = cnt / X;
     const int64_t r = cnt % X;
     const int64_t nbatch = cnt - r;
     PG_TRY(set_slot(b, ids, nbatch, SLOT_NONE));
     PG_TRY(set_slot(b, ids + nbatch, r, SLOT_BUF));
-    bool buffer_changed = r > 0;
+    p.buffer_changed = r > 0;
     // the buffer's members after the remainder joined, ascending ids
     Scratch bufids;
     int64_t nbuf = 0;
@@ -265,18 +265,17 @@ pg_status insert_ids(pg_bdl *b, const int32_t *ids, int64_t cnt) {
                                 cudaMemcpyDeviceToDevice, b->s));
         PG_TRY(set_slot(b, bufids.as<int32_t>(), X, SLOT_NONE));
         q += 1;
-        buffer_changed = true;
+        p.buffer_changed = true;
     }
-    const uint64_t Fn = b->F + (uint64_t)q;
-    const uint64_t consumed = b->F & ~Fn;
-    const uint64_t created = Fn & ~b->F;
+    const uint64_t Fn = F0 + (uint64_t)q;
+    const uint64_t consumed = F0 & ~Fn;
+    const uint64_t created = Fn & ~F0;
     if ((Fn >> MAX_SLOTS) != 0) return fail(PG_EINVAL, "bdl: forest would exceed 62 slots");
     uint64_t taken = 0;
     int64_t pos = 0;
     int top = -1;
     for (int j = 0; j < 64; ++j)
         if ((created >> j) & 1) top = j;
-    pg_tree *made[64] = {};
     for (int j = 0; j < 64; ++j) {
         if (!((created >> j) & 1)) continue;
         const uint64_t below = consumed & ~taken & ((j == 0) ? 0ull : ((1ull << j) - 1));
@@ -297,15 +296,49 @@ pg_status insert_ids(pg_bdl *b, const int32_t *ids, int64_t cnt) {
                                     cudaMemcpyDeviceToDevice, b->s));
         pos += need;
         PG_TRY(set_slot(b, members.as<int32_t>(), total, (int8_t)j));
-        PG_TRY(new_tree(b, members.as<int32_t>(), total, &made[j]));
+        PG_TRY(new_tree(b, members.as<int32_t>(), total, &p.made[j]));
     }
     if (taken != consumed || pos != npool) return fail(PG_EINVAL, "bdl: inconsistent cascade");
+    p.F = Fn;
+    p.consumed = consumed;
+    if (p.buffer_changed) {
+        Scratch bids;
+        PG_TRY(bdl_collect(b, 0, true, bids, &p.buffer_live));
+        if (p.buffer_live > 0) PG_TRY(new_tree(b, bids.as<int32_t>(), p.buffer_live, &p.buffer));
+    }
+    return PG_OK;
+}
+
+// Insert_L, all or nothing.  `drop`: slots whose trees the caller has
+// emptied (erase's under-full trees; their live ids are among ids), released
+// with the consumed trees.  Until every new tree is built nothing but slot
+// codes changes; on an error the new trees are released and the slot codes
+// restored from a copy taken first, so the forest is as before the call.
+pg_status insert_ids(pg_bdl *b, const int32_t *ids, int64_t cnt, uint64_t drop = 0) {
+    if (cnt <= 0 && !drop) return PG_OK;
+    const int64_t nid = b->next_id;
+    Scratch saved;
+    PG_TRY(saved.alloc((size_t)std::max<int64_t>(nid, 1), b->s));
+    if (nid > 0) PG_CUDA(cudaMemcpyAsync(saved.p, b->slot_of, (size_t)nid, cudaMemcpyDeviceToDevice, b->s));
+    InsertPlan p;
+    p.F = b->F & ~drop;
+    const pg_status st = cnt > 0 ? insert_plan(b, ids, cnt, b->F & ~drop, p) : PG_OK;
+    if (st != PG_OK) {
+        for (auto &t : p.made) drop_tree(t);
+        drop_tree(p.buffer);
+        if (nid > 0) cudaMemcpyAsync(b->slot_of, saved.p, (size_t)nid, cudaMemcpyDeviceToDevice, b->s);
+        return st;   // (the message of the first error stands)
+    }
     for (int i = 0; i < 64; ++i)
-        if ((consumed >> i) & 1) drop_tree(b->slot[i]);
+        if (((p.consumed | drop) >> i) & 1) drop_tree(b->slot[i]);
     for (int j = 0; j < 64; ++j)
-        if (made[j]) b->slot[j] = made[j];
-    b->F = Fn;
-    if (buffer_changed) PG_TRY(rebuild_buffer(b));
+        if (p.made[j]) b->slot[j] = p.made[j];
+    b->F = p.F;
+    if (p.buffer_changed) {
+        drop_tree(b->buffer);
+        b->buffer = p.buffer;
+        b->buffer_live = p.buffer_live;
+    }
     b->dirty = true;
     return PG_OK;
 }
@@ -366,26 +399,30 @@ pg_status erase_impl(pg_bdl *b, const float *pts, int64_t cnt) {
     }
     std::vector<int> erased(trees.size());
     PG_TRY(read_small(erased.data(), cnts.p, sizeof(int) * trees.size(), b->s));
+    // the tombstones are in: count them everywhere first, so that a failure
+    // below leaves every live count right (a tree not yet recounted only
+    // keeps subtrees that hold no live point, which searches never match)
     uint64_t destroy = 0;
     for (size_t t = 0; t < trees.size(); ++t) {
-        if (erased[t] == 0) continue;
-        pg_tree *tr = trees[t];
-        tr->live -= erased[t];
+        trees[t]->live -= erased[t];
         if (which[t] < 0) b->buffer_live -= erased[t];
-        pg_status st = PG_OK;
-        PG_DC_DISPATCH(b->dc, st = recount_tree<DCV>(b, tr));
-        PG_TRY(st);
-        if (which[t] >= 0 && 2 * tr->live < capacity(b, which[t])) destroy |= 1ull << which[t];
+        if (erased[t] > 0 && which[t] >= 0 && 2 * trees[t]->live < capacity(b, which[t]))
+            destroy |= 1ull << which[t];
     }
     b->dirty = true;
+    for (size_t t = 0; t < trees.size(); ++t) {
+        if (erased[t] == 0) continue;
+        pg_status st = PG_OK;
+        PG_DC_DISPATCH(b->dc, st = recount_tree<DCV>(b, trees[t]));
+        PG_TRY(st);
+    }
     if (!destroy) return PG_OK;
+    // the erase stands; if the reinsertion fails the under-full trees stay
+    // (every query is still exact) and the error is returned
     Scratch R;
     int64_t nR = 0;
     PG_TRY(bdl_collect(b, destroy, false, R, &nR));
-    for (int i = 0; i < 64; ++i)
-        if ((destroy >> i) & 1) drop_tree(b->slot[i]);
-    b->F &= ~destroy;
-    return insert_ids(b, R.as<int32_t>(), nR);
+    return insert_ids(b, R.as<int32_t>(), nR, destroy);
 }
 
 pg_status refresh_forest(const pg_bdl *cb) {
@@ -449,8 +486,11 @@ pg_status pg_bdl_insert(pg_bdl *b, const float *pts, int64_t cnt, int32_t *out_i
     k_iota<<<grid_of(cnt), BT, 0, b->s>>>(ids.as<int32_t>(), cnt, b->next_id);
     count_launch();
     if (out_ids) PG_CUDA(cudaMemcpyAsync(out_ids, ids.p, sizeof(int32_t) * cnt, cudaMemcpyDeviceToDevice, b->s));
+    const int64_t first = b->next_id;
     b->next_id += cnt;
-    return insert_ids(b, ids.as<int32_t>(), cnt);
+    const pg_status st = insert_ids(b, ids.as<int32_t>(), cnt);
+    if (st != PG_OK) b->next_id = first;   // the ids are handed out again by the next insert
+    return st;
 }
 
 pg_status pg_bdl_erase(pg_bdl *b, const float *pts, int64_t cnt) {
