@@ -725,9 +725,10 @@ def e2e_pipelined(api, torch, dev, pts, leaf, variant, args, stream, barrier, di
     its points from pinned host memory, builds the tree, runs the all-kNN and
     downloads the whole result (indices and distances) to pinned host memory.
     Steps are served the way a server runs independent requests: two host
-    threads, each with its own compute and copy streams and buffers, take
-    every other step, so one thread's uploads, downloads and host waits
-    overlap the other's compute.  Returns the e2e record."""
+    threads, each with its own build, query and copy streams and buffers,
+    take every other step, so one thread's uploads, downloads and host waits
+    overlap the other's compute, and one step's build can run beside the
+    other's query.  Returns the e2e record."""
     import threading
 
     n = len(pts)
@@ -736,7 +737,7 @@ def e2e_pipelined(api, torch, dev, pts, leaf, variant, args, stream, barrier, di
     for w in range(E2E_WORKERS):
         workers.append({
             "compute": torch.cuda.Stream(device=dev), "up": torch.cuda.Stream(device=dev),
-            "down": torch.cuda.Stream(device=dev),
+            "down": torch.cuda.Stream(device=dev), "build": torch.cuda.Stream(device=dev),
             "x": torch.empty((n, DIM), dtype=torch.float32, device=dev),
             "idx": idx if w == 0 else torch.empty_like(idx), "dst": dst if w == 0 else torch.empty_like(dst),
             "h_idx": torch.empty((n, K), dtype=torch.int32).pin_memory(),
@@ -754,15 +755,18 @@ def e2e_pipelined(api, torch, dev, pts, leaf, variant, args, stream, barrier, di
                 wk["x"].copy_(h_in, non_blocking=True)
                 loaded = torch.cuda.Event()
                 loaded.record(up)
-            cs.wait_event(loaded)
+            bs = wk["build"]
+            bs.wait_event(loaded)
+            t = api.pg_tree_build(wk["x"], leaf_size=leaf, stream=bs)
+            built = torch.cuda.Event()
+            built.record(bs)
+            cs.wait_event(built)
             if copied is not None:
                 cs.wait_event(copied)       # the previous result is back on the host
-            t = api.pg_tree_build(wk["x"], leaf_size=leaf, stream=cs)
-            built = torch.cuda.Event()
-            built.record(cs)
             api.pg_knn(t, None, K, out_idx=wk["idx"], out_dist=wk["dst"], stream=cs, variant=variant)
             ready = torch.cuda.Event()
             ready.record(cs)
+            bs.wait_event(ready)            # the tree is freed on its own stream, after the query
             down.wait_event(ready)
             with torch.cuda.stream(down):
                 wk["h_idx"].copy_(wk["idx"], non_blocking=True)
@@ -798,8 +802,8 @@ def e2e_pipelined(api, torch, dev, pts, leaf, variant, args, stream, barrier, di
     e_ms, e_qps = combine_ranks(dist, dev, e0.elapsed_time(e1), n * args.steps, ws)
     return {"value": e_qps / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h_in.numel() * 4), "clocks": clk.summary(),
             "d2h_bytes_per_step": int(workers[0]["h_idx"].numel() * 4 + workers[0]["h_dst"].numel() * 4),
-            "pipelined": f"{E2E_WORKERS} host threads take every other step, each with its own compute and copy "
-                         "streams: one's uploads, downloads and host waits overlap the other's compute"}
+            "pipelined": f"{E2E_WORKERS} host threads take every other step, each with its own build, query and "
+                         "copy streams: one's uploads, downloads and host waits overlap the other's compute"}
 
 
 def run_ours(args):
@@ -925,10 +929,9 @@ def run_ours(args):
 
     # e2e through the public API with host buffers: every step copies its
     # input from pinned host memory and its whole result (indices and
-    # distances) back to pinned host memory.  Steps are pipelined the way a
-    # serving loop runs them: step i+1's input is uploaded on one copy stream
-    # while step i computes, and step i's result goes back on another while
-    # step i+1 computes (two input and two result buffers).
+    # distances) back to pinned host memory.  Two host threads alternate
+    # steps, so one step's copies, host waits and build overlap the other's
+    # query.
     e2e = None
     if not args.no_e2e:
         e2e = e2e_pipelined(api, torch, dev, pts, leaf, variant, args, stream, barrier, dist, ws, idx, dst)
