@@ -76,9 +76,12 @@ typedef struct pg_bdl pg_bdl;     /* one BDL-tree forest (opaque)               
  * spatial-median split, Section 6 "Construction"); a node with at most
  * leaf_size points, with all points equal, or at depth PG_DEPTH_CAP is a leaf.
  * n may be 0 (empty tree).  leaf_size in [1, PG_MAX_LEAF]; n < 2^31.
- * Synchronises with `stream` a few times per build (it reads the root box,
- * the level loop's end flag once the expected depth is reached, the root
- * record and it uploads the tree descriptor), never once per level.
+ * Synchronises with `stream` about twice per build (it reads the root box,
+ * for the finite check, and the level loop's end flag once the expected
+ * depth is reached), never once per level; the root record and the tree
+ * descriptor are written on the device, and the tree's host-side fields
+ * (pg_tree_info, pg_tree_export, range search, k-NN graph) are read back,
+ * with a wait on the tree's stream, by the first such call.
  * Under stream capture (spatial-median split only) it waits on nothing: the
  * level loop is enqueued as a device-driven loop (a conditional WHILE node
  * of the graph being captured, its body captured from a side stream; capture

@@ -813,8 +813,11 @@ struct Builder {
     // deferred: the stream is being captured into a CUDA graph, so nothing
     // may wait on the host; the level loop becomes a device-driven loop and
     // the tree's host-side metadata is read back when it is next needed.
+    // lazy_meta (eager builds): the level loop still reads its end flag, but
+    // the root record and descriptor are written by a kernel and the
+    // host-side metadata is read back when it is next needed, as above.
     static pg_status run(float4 *packed, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t,
-                         bool deferred);
+                         bool deferred, bool lazy_meta = false);
 };
 
 pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
@@ -857,7 +860,7 @@ pg_status grow_nodes(pg_tree *t, int need, cudaStream_t s) {
 
 template <int DC>
 pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, cudaStream_t s, pg_tree *t,
-                           bool deferred) {
+                           bool deferred, bool lazy_meta) {
     constexpr int W = bucket_w(DC);
     // Split segments hold more than `leaf` points and are disjoint, so a level
     // has at most 2*floor(n/(leaf+1)) segments.
@@ -1107,12 +1110,15 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
     t->depth = hctl[CTL_LEVELS];
     t->root_ref = 0;
     t->root_cnt = root_split ? 0 : (int)n;
+    Scratch sRec;
+    int *rec = nullptr;
+    if (fin_total > 0 || lazy_meta) {
+        PG_TRY(sRec.alloc(sizeof(int) * 3, s));
+        rec = sRec.as<int>();
+        PG_TRY(fill_words(rec, 0u, 3, s));
+    }
     if (fin_total > 0) {
         PG_CUDA(cudaFuncSetAttribute(k_finish<DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fin_smem));
-        Scratch sRec;
-        PG_TRY(sRec.alloc(sizeof(int) * 3, s));
-        int *rec = sRec.as<int>();
-        PG_TRY(fill_words(rec, 0u, 3, s));
         {
             KTimer kt("build_finish", s);
             k_finish<DC><<<std::min(fin_total, num_sms() * 3), FIN_NT, fin_smem, s>>>(
@@ -1121,12 +1127,14 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
             count_launch();
         }
         PG_TRY(check_launch("build finish"));
-        int h[3];
-        PG_TRY(read_small(h, rec, sizeof(int) * 3, s));
-        t->depth = std::max(t->depth, h[2]);
-        if (!root_split) {   // the whole tree was one finisher segment
-            t->root_ref = h[0];
-            t->root_cnt = h[1];
+        if (!lazy_meta) {
+            int h[3];
+            PG_TRY(read_small(h, rec, sizeof(int) * 3, s));
+            t->depth = std::max(t->depth, h[2]);
+            if (!root_split) {   // the whole tree was one finisher segment
+                t->root_ref = h[0];
+                t->root_cnt = h[1];
+            }
         }
     }
     // leaves of finisher segments were recorded by the finisher; the level
@@ -1142,6 +1150,15 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
         t->bucket = P;
         sP1.p = nullptr;           // ownership moves to the tree
         dfree(P0, s);
+    }
+    if (lazy_meta) {
+        if (!t->desc) PG_TRY(dalloc_n(&t->desc, 1, s));
+        if (!t->meta) PG_TRY(dalloc_n(&t->meta, (size_t)kTreeMetaWords, s));
+        k_tree_meta<DC><<<1, 32, 0, s>>>(ctl, rec, box, (int)n, t->bucket, t->nodes, t->parent, t->leaf_parent,
+                                         t->desc, t->meta);
+        count_launch();
+        PG_TRY(check_launch("build descriptor"));
+        t->meta_pending = true;
     }
     return PG_OK;
 }
@@ -1349,12 +1366,14 @@ static pg_status build_from(const float *src, const int32_t *rows, const int32_t
             return fail(PG_EINVAL, "points must have finite coordinates");
         }
     }
-    PG_DC_SWITCH(dc, st = Builder<DCV>::run(packed, box.as<int>(), n, leaf, rule, s, t, false));
+    // builds of pg_tree_build (allow_deferred) leave the root record and the
+    // descriptor to a kernel: the host does not wait for the finisher
+    PG_DC_SWITCH(dc, st = Builder<DCV>::run(packed, box.as<int>(), n, leaf, rule, s, t, false, allow_deferred));
     if (st != PG_OK) {
         if (t->bucket != packed) dfree(packed, s);
         return st;
     }
-    return tree_upload_desc(t);
+    return t->meta_pending ? PG_OK : tree_upload_desc(t);
 }
 
 pg_status build_rows(const float *pts, int64_t n, int dim, int leaf, int rule, cudaStream_t s, pg_tree *t) {
