@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const floa
                                                            const int *__restrict__ T, unsigned *__restrict__ tsum,
                                                            unsigned *__restrict__ twords,
                                                            const int *__restrict__ pflag = nullptr) {
+    pdl_wait();
+    pdl_trigger();
     if (*T == 0) return;
     __shared__ unsigned rowsum[PT_WR], fword[PT_WR], rword[PT_WR];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -202,6 +204,8 @@ __global__ void __launch_bounds__(PT_THREADS) k_part_tiles(int64_t n, const floa
 // Segmented exclusive scan over the tiles (one block).
 __global__ void __launch_bounds__(1024) k_part_carry(unsigned *__restrict__ tsum, int ntiles, const int *__restrict__ T,
                                                      int *__restrict__ ctl, const int *__restrict__ fin_total, int level) {
+    pdl_wait();
+    pdl_trigger();
     // end of the level: advance the control block (nothing after this kernel
     // in the level reads it); level < 0: the index is kept in the block
     if (threadIdx.x == 0 && !ctl[CTL_DONE]) {
@@ -459,6 +463,8 @@ __global__ void __launch_bounds__(HEAD_NT) k_level_head(
     int *__restrict__ nx_parent, int *__restrict__ nx_side, int *__restrict__ nx_depth, int *__restrict__ nx_lo,
     int *__restrict__ nx_hi, int *__restrict__ fin_flag, int *__restrict__ fin_rank, Segs fin,
     int *__restrict__ n_parent, int *__restrict__ roots, int fin_link) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int wsum[32];
     const int S = ctl[CTL_DONE] ? 0 : min(ctl[CTL_S], S_max);
     for (int x = threadIdx.x; x < S_max; x += HEAD_NT)
@@ -480,13 +486,20 @@ template <int DC>
 pg_status level_segments(int S_max, int *ctl, const Segs &cur, const Segs &nxt, int leaf, int thr, int *split_flag,
                          int *split_rank, int *sdim, float *sval, int *fin_flag, int *fin_rank, const Segs &fin,
                          float4 *nodes, int *n_sdim, float *n_sval, int2 *n_range, int *n_parent, int *roots,
-                         int fin_link, int *scan_ws, cudaStream_t s) {
+                         int fin_link, int *scan_ws, cudaStream_t s, bool pdl = false) {
     if (S_max <= kHeadMax) {
-        k_level_head<DC><<<1, HEAD_NT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth,
-                                               cur.lo, cur.hi, leaf, PG_DEPTH_CAP, thr, split_flag, split_rank,
-                                               sdim, sval, nodes, n_sdim, n_sval, n_range, nxt.parent, nxt.side,
-                                               nxt.depth, nxt.lo, nxt.hi, fin_flag, fin_rank, fin, n_parent, roots,
-                                               fin_link);
+        if (pdl) {
+            PG_CUDA(launch_pdl(k_level_head<DC>, 1, HEAD_NT, 0, s, S_max, ctl, cur.start, cur.end, cur.parent,
+                               cur.side, cur.depth, cur.lo, cur.hi, leaf, PG_DEPTH_CAP, thr, split_flag, split_rank,
+                               sdim, sval, nodes, n_sdim, n_sval, n_range, nxt.parent, nxt.side, nxt.depth, nxt.lo,
+                               nxt.hi, fin_flag, fin_rank, fin, n_parent, roots, fin_link));
+        } else {
+            k_level_head<DC><<<1, HEAD_NT, 0, s>>>(S_max, ctl, cur.start, cur.end, cur.parent, cur.side, cur.depth,
+                                                   cur.lo, cur.hi, leaf, PG_DEPTH_CAP, thr, split_flag, split_rank,
+                                                   sdim, sval, nodes, n_sdim, n_sval, n_range, nxt.parent, nxt.side,
+                                                   nxt.depth, nxt.lo, nxt.hi, fin_flag, fin_rank, fin, n_parent,
+                                                   roots, fin_link);
+        }
         count_launch();
         return PG_OK;
     }
@@ -523,6 +536,8 @@ __global__ void __launch_bounds__(PT_THREADS, DC <= 4 ? 8 : 4) k_part(int64_t n,
                                                      const unsigned *__restrict__ twords, int *__restrict__ nx_start,
                                                      int *__restrict__ nx_end, int *__restrict__ nx_lo,
                                                      int *__restrict__ nx_hi, const int *__restrict__ T) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int W = bucket_w(DC);
     if (*T == 0) return;
     __shared__ int tag[kBoxSlots];
@@ -1052,7 +1067,7 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
         const int S_max = (int)std::min<int64_t>((int64_t)1 << std::min(level, 30), S_bound);
         PG_TRY(level_segments<DC>(S_max, ctl, cur, nxt, leaf, fin_max, split_flag, split_rank, sdim, sval, fin_flag,
                                   fin_rank, fin, t->nodes, t->split_dim, t->split_val, t->node_range, t->parent,
-                                  nullptr, 0, nullptr, s));
+                                  nullptr, 0, nullptr, s, rule != PG_SPLIT_OBJECT));
         const int *T = split_rank + S_max;
         if (rule == PG_SPLIT_OBJECT) {
             const int g = ceil_div_i(n, BT);
@@ -1081,13 +1096,16 @@ pg_status Builder<DC>::run(float4 *P0, int *box, int64_t n, int leaf, int rule, 
                                                      split_rank, tsum, twords, nxt.start, nxt.end, nxt.lo, nxt.hi, T);
             for (int c = 0; c < 5; ++c) count_launch();
         } else {
-            k_part_tiles<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, seg_of, split_flag, sdim, sval, T, tsum, twords);
-            k_part_carry<<<1, 1024, 0, s>>>(tsum, ntiles, T, ctl, fin_rank + S_max, level);
+            // one chain of dependent launches per level (head, tiles, carry,
+            // move): each may be scheduled while the one before finishes
+            PG_CUDA(launch_pdl(k_part_tiles<DC>, ntiles, PT_THREADS, 0, s, n, P, seg_of, split_flag, sdim, sval, T,
+                               tsum, twords, nullptr));
+            PG_CUDA(launch_pdl(k_part_carry, 1, 1024, 0, s, tsum, ntiles, T, ctl, fin_rank + S_max, level));
             count_launch();
             count_launch();
             KTimer kt("build_scatter", s);
-            k_part<DC><<<ntiles, PT_THREADS, 0, s>>>(n, P, Q, seg_of, seg_of_nx, cur.start, cur.end, split_flag,
-                                                     split_rank, tsum, twords, nxt.start, nxt.end, nxt.lo, nxt.hi, T);
+            PG_CUDA(launch_pdl(k_part<DC>, ntiles, PT_THREADS, 0, s, n, P, Q, seg_of, seg_of_nx, cur.start, cur.end,
+                               split_flag, split_rank, tsum, twords, nxt.start, nxt.end, nxt.lo, nxt.hi, T));
             count_launch();
         }
         PG_TRY(check_launch("build level"));

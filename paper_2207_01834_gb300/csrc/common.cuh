@@ -82,6 +82,30 @@ pg_status read_small(void *host_dst, const void *dev_src, size_t bytes, cudaStre
 inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 int num_sms();
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be
+// scheduled while the kernel before it in the stream is still running; it
+// calls pdl_wait() before touching anything, which returns once every kernel
+// before it has completed and its writes are visible (a no-op for a normal
+// launch).  pdl_trigger() then lets the kernel after it be scheduled early,
+// so the launch latency between dependent kernels is hidden.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... Exp, class... Act>
+cudaError_t launch_pdl(void (*kernel)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Act &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Exp>(args)...);
+}
+
 // ---------------------------------------------------------------- layout
 // Coordinates stored per point: the dimension class DC >= dim (zero padded).
 inline int dim_class(int dim) {
