@@ -202,3 +202,16 @@ def test_automatic_traversal_choice_without_a_device(lib):
     finally:
         lib.pg_knn_tune_set(7, 16, 0, 0)
     assert lib.pg_knn_tune_set(3, 10, 1, 6) != 0     # not a traversal
+
+
+def test_traversal_constants_match_the_header():
+    """The binding's KNN_* numbers are the header's PG_KNN_* values, and every
+    traversal the header defines is in KNN_VARIANTS."""
+    from paper_2207_01834_gb300 import _lib
+
+    text = open(os.path.join(ROOT, "include", "pargeo_gpu.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define PG_(KNN_\w+)\s+(\d+)", text)}
+    assert defs["KNN_AUTO"] == 0 and len(defs) >= 6
+    for name, value in defs.items():
+        assert getattr(_lib, name) == value, name
+    assert sorted(_lib.KNN_VARIANTS) == sorted(v for k, v in defs.items() if k != "KNN_AUTO")
